@@ -1,0 +1,173 @@
+/*
+ * dgt.h -- discrete Gabor transform on a nonseparable lattice, CUDA (sm_103a) library.
+ *
+ * The transform (Wiesmeyr, Holighaus, Soendergaard, "Efficient algorithms for discrete
+ * Gabor transforms on a nonseparable lattice", Section 2.1, eq. DGT):
+ *
+ *   c(m, n) = sum_{l<L} f(l) conj(g(l - a n)) exp(-2 pi i l (m + w(n)) / M),
+ *   w(n)    = ((n * lambda1) mod lambda2) / lambda2,      m < M,  n < N = L / a,
+ *
+ * i.e. the samples of the short-time Fourier transform on the lattice
+ * {(a n, m b + s(n))}, b = L / M, s(n) = (n s) mod b, s = b lambda1 / lambda2
+ * (Prop. lattNF).  Synthesis is the adjoint (Section 2.1, inversion formula):
+ *
+ *   f(l) = sum_{m,n} c(m, n) gamma(l - a n) exp(+2 pi i l (m + w(n)) / M).
+ *
+ * Conventions for every entry point
+ *   - Buffers passed to dgt_exec / idgt_exec / the window routines are DEVICE pointers
+ *     on the current CUDA device, owned by the caller, and must not overlap.
+ *   - Signals are [batch][L]; real signals are float32/float64, complex signals are
+ *     interleaved (re, im) pairs of the plan's precision.  Coefficients are
+ *     [batch][N][M] complex, m contiguous (column c(., n) is contiguous).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is enqueued
+ *     asynchronously; no entry point synchronises the stream unless stated.
+ *   - Return value: DGT_OK or a dgt_status code; dgt_last_error() gives a message.
+ *     Asynchronous device faults surface at the next call that synchronises.
+ *   - A plan is not thread-safe: use one plan per host thread or serialise calls.
+ */
+#ifndef DGT_H
+#define DGT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgt_plan_s* dgt_plan_t;
+
+typedef enum {
+    DGT_OK = 0,
+    DGT_ERR_ARG = 1,          /* invalid argument (null pointer, bad enum, lambda1 >= lambda2, ...) */
+    DGT_ERR_LENGTH = 2,       /* L is not a multiple of lambda2 * lcm(a, M) (Prop. minsig) */
+    DGT_ERR_NOT_FRAME = 3,    /* a Gram block is singular or ill-conditioned: no dual / tight window */
+    DGT_ERR_CUDA = 4,         /* a CUDA call failed */
+    DGT_ERR_OOM = 5,          /* device allocation failed */
+    DGT_ERR_TIMEOUT = 6,      /* a bounded device wait expired */
+    DGT_ERR_UNSUPPORTED = 7   /* valid lattice outside this build's limits (FFT length, Gram block size) */
+} dgt_status;
+
+typedef enum {
+    DGT_ROUTE_AUTO = 0,       /* FIR windows: FIR route; full windows: shear if s0 = 0, else coset */
+    DGT_ROUTE_COSET = 1,      /* union of lambda2 separable lattices (Prop. mwindec, eq. mw_phases) */
+    DGT_ROUTE_SHEAR = 2,      /* chirps + separable DGT + phase / reindex (Theorem shearform, Algorithm 1) */
+    DGT_ROUTE_FIR = 3         /* weighted overlap-add with a short window (eq. rect-flops-FIR) */
+} dgt_route;
+
+typedef enum { DGT_F32 = 0, DGT_F64 = 1 } dgt_precision;
+
+typedef enum {
+    DGT_WINDOW_FULL = 0,      /* len == L samples, g(0) first */
+    DGT_WINDOW_FIR = 1        /* len <= L/2 taps; tap t sits at time (t - center) mod L */
+} dgt_window_kind;
+
+typedef enum {
+    DGT_SYN_ADJOINT = 0,      /* window g itself: the adjoint C_g^* */
+    DGT_SYN_DUAL = 1,         /* canonical dual S^{-1} g: perfect reconstruction */
+    DGT_SYN_TIGHT = 2         /* canonical tight S^{-1/2} g, with the analysis done by the same tight window */
+} dgt_synthesis_window;
+
+typedef struct {
+    int kind;                 /* dgt_window_kind */
+    int64_t len;              /* number of samples / taps */
+    int64_t center;           /* FIR only: index of the tap at time 0 */
+    const double* data;       /* HOST memory, float64: len reals, or len interleaved complex pairs */
+    int is_real;              /* 1: data holds len reals */
+} dgt_window;
+
+typedef struct {
+    int64_t L, a, M, lambda1, lambda2, b, N, s;
+    int route;                /* resolved route (never DGT_ROUTE_AUTO) */
+    int precision;
+    int64_t s0, s1, b_r;      /* shear parameters chosen for the shear route (0 otherwise) */
+    int64_t sep_a, sep_M;     /* separable lattice run by the Zak engine (coset: lambda2 a, M) */
+    int64_t c, d, p, q;       /* its constants, eqs. (cd, pq) */
+    int64_t n_windows;        /* window factors held (lambda2 for coset, 1 otherwise) */
+    int64_t fir_len;          /* FIR taps (FIR route) */
+} dgt_plan_info;
+
+/* Create a plan for the lattice (L, a, M, lambda1/lambda2) and window g.
+ * Checks feasibility (Prop. minsig: L multiple of lambda2 * lcm(a, M)), chooses the route,
+ * finds the shear parameters (Theorem shearform, eq. modcond) and precomputes on the device
+ * the window's factorisation.  Copies g; *plan receives the handle.  Synchronises `stream`.
+ * Errors: DGT_ERR_ARG, DGT_ERR_LENGTH, DGT_ERR_UNSUPPORTED, DGT_ERR_OOM, DGT_ERR_CUDA. */
+int dgt_plan_create(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t lambda1, int64_t lambda2,
+                    const dgt_window* g, int route, int precision, void* stream);
+
+/* Copy the resolved plan parameters into *info. */
+int dgt_plan_get_info(dgt_plan_t plan, dgt_plan_info* info);
+
+/* Replace the window with a DEVICE buffer of the plan's precision (same kind and length as at
+ * creation; real or interleaved complex) and recompute its factorisation.  Invalidates the
+ * cached dual / tight windows.  Asynchronous on `stream`. */
+int dgt_plan_set_window(dgt_plan_t plan, const void* g_dev, int is_real, void* stream);
+
+/* Analysis: c = C_g f for `batch` signals (Section 2.1, eq. DGT; coset route eqs. mw_frop /
+ * mw_phases, shear route Algorithm 1, FIR route eq. rect-flops-FIR).
+ * f: [batch][L] real (f_is_real = 1) or complex; c: [batch][N][M] complex.
+ * Uses the plan's workspace (grown on demand with cudaMalloc; see dgt_exec_ws). */
+int dgt_exec(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* stream);
+
+/* Synthesis: f = C_gamma^* c, gamma chosen by `which_window` (dgt_synthesis_window).
+ * The dual / tight window is computed on first use (Gram blocks in float64) and cached.
+ * f_real_out = 1 writes the real part only (float of the plan precision). */
+int idgt_exec(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
+              void* stream);
+
+/* Workspace needed by dgt_exec_ws / idgt_exec_ws for `batch` signals, in bytes. */
+int dgt_workspace_bytes(dgt_plan_t plan, int64_t batch, size_t* bytes);
+
+/* As dgt_exec / idgt_exec, with a caller-provided device workspace of at least
+ * dgt_workspace_bytes(batch) bytes, 256-byte aligned.  These never allocate (the dual /
+ * tight window of idgt_exec_ws must already be cached by dgt_window_dual / _tight). */
+int dgt_exec_ws(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* workspace,
+                void* stream);
+int idgt_exec_ws(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
+                 void* workspace, void* stream);
+
+/* Canonical dual window S^{-1} g (eq. frameop) into gamma_out: L complex values of the plan's
+ * precision (device).  Computed through the Zak-domain Gram blocks of the coset decomposition
+ * (eq. mw_frop), inverted in float64; FIR windows no longer than M use the diagonal form.
+ * DGT_ERR_NOT_FRAME if a block is singular.  Synchronises `stream`. */
+int dgt_window_dual(dgt_plan_t plan, void* gamma_out, void* stream);
+
+/* Canonical tight window S^{-1/2} g, as dgt_window_dual. */
+int dgt_window_tight(dgt_plan_t plan, void* gt_out, void* stream);
+
+/* Window gradient of a real-valued loss l(c): given G = dl/dRe(c) + i dl/dIm(c) for every
+ * coefficient of `batch` signals f, writes grad_g = sum over the batch of
+ * sum_n f(. + a n) conj(U_n(. + a n)), U_n(l) = sum_m G(m,n) exp(+2 pi i l (m + w(n))/M)
+ * (L values, real part if grad_real).  The signal gradient is idgt_exec(..., DGT_SYN_ADJOINT)
+ * applied to G.  Full-length windows only. */
+int dgt_grad_window(dgt_plan_t plan, const void* f, int f_is_real, const void* G, void* grad_g, int grad_real,
+                    int64_t batch, void* stream);
+
+/* Log-magnitude loss helper: loss_b = sum log(|c|^2 + eps) per signal (float64, device array of
+ * `batch`), and G = 2 c / (|c|^2 + eps) (device, may be NULL). */
+int dgt_logmag_loss(dgt_plan_t plan, const void* c, void* G, double* loss_dev, double eps, int64_t batch,
+                    void* stream);
+
+/* Bytes of device memory owned by the plan (tables, window factors, cached windows, workspace). */
+int dgt_plan_bytes(dgt_plan_t plan, size_t* bytes);
+
+/* Synchronise `stream` and report a pending asynchronous CUDA error as DGT_ERR_CUDA. */
+int dgt_sync(void* stream);
+
+/* Release the plan and its device memory (synchronises the device first). */
+void dgt_plan_destroy(dgt_plan_t plan);
+
+/* Human-readable status name, and the message of the last error on this host thread. */
+const char* dgt_strerror(int status);
+const char* dgt_last_error(void);
+
+/* Building block check: `howmany` contiguous complex transforms of length n (device buffers),
+ * direction -1 (forward) or +1 (unnormalised inverse), precision DGT_F32 / DGT_F64. */
+int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, void* out, int64_t howmany,
+                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGT_H */

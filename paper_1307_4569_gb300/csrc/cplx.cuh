@@ -1,0 +1,69 @@
+// Complex arithmetic on float2 / double2 and exact phase tables.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgt {
+
+template <typename T> struct CT;
+template <> struct CT<float> { using type = float2; };
+template <> struct CT<double> { using type = double2; };
+template <typename T> using cplx = typename CT<T>::type;
+
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { using type = float; };
+template <> struct RealOf<double2> { using type = double; };
+
+__host__ __device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
+__host__ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
+
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// a * conj(b)
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
+// multiply by +i (DIR=+1) or -i (DIR=-1)
+template <int DIR, typename C> __host__ __device__ __forceinline__ C mul_i(C a) {
+    C r;
+    if (DIR > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+    return r;
+}
+
+// exp(2 pi i e / den) for integer e (any sign), from a two-level table built on the
+// host in double precision: hi[k] = exp(2 pi i k S / den), lo[r] = exp(2 pi i r / den),
+// e mod den = k S + r.  Two rounded factors, so the result is accurate to a few ulp of
+// the working precision, independent of the size of den.
+template <typename C> struct CisTable {
+    const C* hi;
+    const C* lo;
+    int64_t den;
+    int64_t S;
+    __device__ __forceinline__ C operator()(int64_t e) const {
+        int64_t r = e % den;
+        if (r < 0) r += den;
+        const int64_t k = r / S;
+        const int64_t m = r - k * S;
+        return cmul(__ldg(hi + k), __ldg(lo + m));
+    }
+};
+
+// (x * y) mod m for 0 <= x, y < m <= 2^32
+__host__ __device__ __forceinline__ uint64_t mulmod(uint64_t x, uint64_t y, uint64_t m) { return (x * y) % m; }
+__host__ __device__ __forceinline__ int64_t posmod(int64_t x, int64_t m) {
+    int64_t r = x % m;
+    return r < 0 ? r + m : r;
+}
+
+}  // namespace dgt

@@ -1,0 +1,150 @@
+// Internal interface between the host planner (plan.cpp) and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cplx.cuh"
+#include "fft.cuh"
+
+namespace dgt {
+
+// Threads per CTA of the FFT-tile kernels, and the shared memory one CTA may use.
+constexpr int kThreads = 256;
+constexpr int kThreadsBig = 512;
+constexpr size_t kSmemBudget = 200 * 1024;
+inline int threads_for(int64_t elems) { return elems >= 4096 ? kThreadsBig : kThreads; }
+
+struct FftRef {                 // one FFT length: radix plan + device twiddle table
+    FftPlanDev pl;
+    const void* tw;             // cplx<T>[n], tw[e] = exp(-2 pi i e / n)
+};
+
+// Separable lattice on which the Zak/polyphase engine runs (eqs. cd, pq).
+struct SepGeom {
+    int64_t L, a, M, b, N, c, d, p, q, K0;   // K0 = L / d = c p q
+};
+
+// Post-processing of the channel FFT (analysis) / pre-processing of its adjoint.
+enum PostMode : int {
+    POST_PLAIN = 0,     // separable lattice: row n -> column n
+    POST_COSET = 1,     // row (j, nt) -> column lam2 nt + j, phase exp(-2 pi i nt at sigma_j / L)
+    POST_SHEAR0 = 2,    // time shear only (s0 = 0): phase E_n, cyclic rotation of the column
+    POST_SHEAR1 = 3,    // frequency shear (s0 != 0): phase E(k, m) and reindex of both indices
+};
+
+template <typename C> struct PostParams {
+    int mode;
+    int64_t L, M, N, b, a;            // output (nonseparable) lattice
+    int64_t lam2, at;                 // coset
+    const int64_t* sigma;             // coset frequency shifts sigma_j (device, J entries)
+    int64_t s1a_modL;                 // shear0: (s1 * a) mod L ; rotation rot_n = floor(((-s1 a n) mod L)/b)
+    int64_t C1_2N;                    // shear0: C1 mod 2N
+    // shear1 (Algorithm 1, s0 != 0), all reduced modulo 2N or L as used
+    int64_t Nr, C1, C2_N, C1_2N_, C2_2N, C3_2N, C4_2N, C5_2N, s1ar_L, C6_L;
+    CisTable<C> cisL;                 // exp(2 pi i e / L)
+    CisTable<C> cis2N;                // exp(2 pi i e / (2N)) = exp(pi i e / N)
+};
+
+// Signal pre-processing inside the factorisation / FFT_L passes.
+enum PreMode : int {
+    PRE_NONE = 0,
+    PRE_CHIRP = 1,      // x(l) * exp(pi i (s l^2 (L+1) mod 2L) / L)   (pchirp(L, s))
+};
+
+template <typename C> struct ChirpParams {
+    int mode;
+    int64_t L;
+    int64_t s_2L;                     // s mod 2L
+    int conj;                         // multiply by the conjugate chirp
+    CisTable<C> cis2L;                // exp(2 pi i e / (2L))
+};
+
+// ------------------------------------------------------------------------------------
+// launchers (templated on the real type T; explicitly instantiated in the .cu files)
+// ------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_zak_fwd(const void* src, int src_real, int64_t src_bstride, cplx<T>* zf, int64_t zf_bstride,
+                           int64_t L, int64_t d, const FftRef& fd, const ChirpParams<cplx<T>>& pre, int64_t B,
+                           cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T>* y, const SepGeom& g,
+                             const FftRef& fd, int64_t B, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const FftRef& fm,
+                            const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st);
+
+// adjoint chain (synthesis)
+template <typename T>
+cudaError_t launch_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const FftRef& fm,
+                            const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
+                                const FftRef& fd, int64_t B, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_zak_inv(const cplx<T>* zf, int64_t zf_bstride, void* dst, int dst_real, int64_t dst_bstride,
+                           int64_t L, int64_t d, const FftRef& fd, const ChirpParams<cplx<T>>& post, T scale,
+                           int64_t B, cudaStream_t st);
+
+// window gradient through the factorisation: V_j[xi][col] accumulated over the batch
+template <typename T>
+cudaError_t launch_fft_grad_window(const cplx<T>* y, const cplx<T>* zf, int64_t J, cplx<T>* v, const SepGeom& g,
+                                   const FftRef& fd, int64_t B, cudaStream_t st);
+
+// four-step FFT of length L = L1 * L2 (frequency-shear branch and window set-up)
+template <typename T>
+cudaError_t launch_fftL_cols(const void* src, int src_real, cplx<T>* tmp, int64_t L1, int64_t L2, int dir,
+                             const FftRef& f1, const ChirpParams<cplx<T>>& pre, const CisTable<cplx<T>>& cisL,
+                             int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fftL_rows(const cplx<T>* tmp, void* dst, int dst_real, int64_t L1, int64_t L2, int dir,
+                             const FftRef& f2, const ChirpParams<cplx<T>>& post, T scale, int64_t B,
+                             cudaStream_t st);
+
+// FIR (weighted overlap-add) path
+template <typename C> struct FirParams {
+    int64_t L, a, M, N, lam1, lam2, Lg, center;
+    const C* taps;                    // Lg taps of the analysis / synthesis window
+    CisTable<C> cisLM;                // exp(2 pi i e / (lam2 M))
+    int64_t cols;                     // time positions per CTA
+};
+template <typename T>
+cudaError_t launch_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp,
+                                const FftRef& fm, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>* seams,
+                                 const FirParams<cplx<T>>& fp, const FftRef& fm, int64_t B, cudaStream_t st);
+template <typename C>
+int64_t fir_seam_elems(const FirParams<C>& fp);
+
+// elementwise helpers
+template <typename T>
+cudaError_t launch_coset_windows(const cplx<T>* g, cplx<T>* gj, int64_t L, int64_t a, int64_t J, const int64_t* sigma,
+                                 const CisTable<cplx<T>>& cisL, cudaStream_t st);
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const void* in, int in_real, cplx<Tout>* out, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_grad_window_combine(const cplx<T>* wj, void* grad, int grad_real, int64_t L, int64_t a, int64_t J,
+                                       const int64_t* sigma, const CisTable<cplx<T>>& cisL, cudaStream_t st);
+template <typename T>
+cudaError_t launch_logmag(const cplx<T>* c, cplx<T>* u, double* partial, int64_t n, T eps, int64_t B,
+                          cudaStream_t st);
+
+// dual / tight window Gram blocks (float64)
+cudaError_t launch_gram_solve(const double2* zg, int64_t J, double2* zout, const SepGeom& g, int tight,
+                              int* status, cudaStream_t st);
+cudaError_t launch_fir_dual(const double2* taps, double2* out, int64_t Lg, int64_t a, int64_t M, int tight,
+                            int* status, cudaStream_t st);
+
+// FFT self-test (batched transforms along contiguous rows)
+template <typename T>
+cudaError_t launch_fft_rows_test(const cplx<T>* in, cplx<T>* out, const FftRef& f, int dir, int64_t rows,
+                                 cudaStream_t st);
+
+// CTA sizing: largest FFT tile (elements, two ping-pong buffers) that fits the budget
+template <typename T> constexpr int64_t tile_cap() { return (int64_t)(kSmemBudget / (2 * sizeof(cplx<T>))); }
+
+}  // namespace dgt

@@ -1,0 +1,507 @@
+// FIR (weighted overlap-add) path, window set-up, Gram blocks of the dual / tight windows,
+// the window-gradient combination and the log-magnitude loss.
+#include "engine.h"
+
+#include <algorithm>
+
+namespace dgt {
+
+template <typename C> __device__ __forceinline__ C load_any2(const void* p, int is_real, int64_t i) {
+    using R = typename RealOf<C>::type;
+    if (is_real) return mk(reinterpret_cast<const R*>(p)[i], (R)0);
+    return reinterpret_cast<const C*>(p)[i];
+}
+
+static size_t g_smem_optin2 = 0;
+template <typename K> static cudaError_t prep_smem2(K kernel, size_t bytes) {
+    if (g_smem_optin2 == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        g_smem_optin2 = (size_t)v;
+    }
+    if (bytes > g_smem_optin2) return cudaErrorInvalidValue;
+    if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+// =====================================================================================
+// FIR analysis: for a chunk of `cols` time positions n of one signal,
+//   h_n(k) = sum_{x : (a n + x) mod M = k} f(a n + x) conj(g(x)) e^{-2 pi i (a n + x) w(n) / M}
+//   c(., n) = FFT_M(h_n)          (eq. DGT folded modulo M; cost of eq. rect-flops-FIR)
+// x runs over the window support [-center, Lg - center).  grid (chunks, B)
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(kThreadsBig) fir_analysis_kernel(const void* __restrict__ f, int f_real,
+                                                                   cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
+                                                                   FftPlanDev pl, const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = pl.n, pitch = M + 1;
+    const int64_t b = blockIdx.y;
+    const int64_t n0 = (int64_t)blockIdx.x * fp.cols;
+    const int nc = (int)min(fp.cols, fp.N - n0);
+    const int64_t S = fp.a * (nc - 1) + fp.Lg;                // segment length
+    C* rows = reinterpret_cast<C*>(smem_raw);
+    C* seg = rows + 2 * (size_t)fp.cols * pitch;
+    const int64_t lstart = fp.a * n0 - fp.center;
+    for (int64_t t = threadIdx.x; t < S; t += blockDim.x) {
+        const int64_t l = posmod(lstart + t, fp.L);
+        seg[t] = load_any2<C>(f, f_real, b * fp.L + l);
+    }
+    __syncthreads();
+    const int64_t LM = fp.lam2 * fp.M;
+    for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
+        const int r = e / M, k = e % M;
+        const int64_t n = n0 + r;
+        const int64_t ln = fp.a * n - fp.center;              // time of tap 0
+        const int64_t wn = (n * fp.lam1) % fp.lam2;
+        int64_t t = posmod((int64_t)k - ln, fp.M);            // first tap folding onto k
+        C h = mk((T)0, (T)0);
+        for (; t < fp.Lg; t += fp.M) {
+            const int64_t l = posmod(ln + t, fp.L);
+            C v = cmulc(seg[fp.a * r + t], __ldg(fp.taps + t));
+            if (wn) v = cmul(v, fp.cisLM(-(int64_t)mulmod((uint64_t)(l % LM), (uint64_t)wn, (uint64_t)LM)));
+            h = cadd(h, v);
+        }
+        rows[r * pitch + k] = h;
+    }
+    __syncthreads();
+    const C* res = fft_tile<-1, false>(rows, rows + fp.cols * pitch, pl, nc, 1, pitch, tw);
+    for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
+        const int r = e / M, m = e % M;
+        c[(b * fp.N + n0 + r) * fp.M + m] = res[r * pitch + m];
+    }
+}
+
+template <typename C> int64_t fir_seam_elems(const FirParams<C>& fp) {
+    const int64_t ov = std::max<int64_t>(0, fp.Lg - fp.a);
+    return (fp.N / fp.cols) * 2 * ov;
+}
+template int64_t fir_seam_elems<float2>(const FirParams<float2>&);
+template int64_t fir_seam_elems<double2>(const FirParams<double2>&);
+
+template <typename T>
+cudaError_t launch_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp,
+                                const FftRef& fm, int64_t B, cudaStream_t st) {
+    using C = cplx<T>;
+    const int64_t S = fp.a * (fp.cols - 1) + fp.Lg;
+    const size_t smem = sizeof(C) * (2 * (size_t)fp.cols * (fp.M + 1) + S);
+    if (smem > kSmemBudget) return cudaErrorInvalidValue;
+    auto k = fir_analysis_kernel<T>;
+    cudaError_t e = prep_smem2(k, smem);
+    if (e != cudaSuccess) return e;
+    const int thr = threads_for(fp.cols * fp.M);
+    dim3 grid((unsigned)((fp.N + fp.cols - 1) / fp.cols), (unsigned)B);
+    k<<<grid, thr, smem, st>>>(f, f_real, c, fp, fm.pl, (const C*)fm.tw);
+    return cudaGetLastError();
+}
+
+// =====================================================================================
+// FIR synthesis (adjoint): per chunk of `cols` columns, unnormalised inverse FFT_M of each
+// column, then for every sample of the chunk's segment gather
+//   f(l) = sum_n gamma(l - a n) e^{+2 pi i l w(n)/M} h_n(l mod M)
+// Samples reached only by this chunk's columns are stored; the two seams of Lg - a samples
+// shared with the neighbouring chunks go to a seam buffer and are summed by fir_seams.
+// Requires N % cols == 0 and a * cols >= Lg - a (host-checked).
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(kThreadsBig) fir_synthesis_kernel(const cplx<T>* __restrict__ c, void* __restrict__ f,
+                                                                    int f_real, cplx<T>* __restrict__ seams,
+                                                                    FirParams<cplx<T>> fp, FftPlanDev pl,
+                                                                    const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using R = T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = pl.n, pitch = M + 1;
+    const int64_t b = blockIdx.y;
+    const int64_t chunk = blockIdx.x;
+    const int64_t nchunks = gridDim.x;
+    const int64_t n0 = chunk * fp.cols;
+    const int nc = (int)fp.cols;
+    C* rows = reinterpret_cast<C*>(smem_raw);
+    for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
+        const int r = e / M, m = e % M;
+        rows[r * pitch + m] = c[(b * fp.N + n0 + r) * fp.M + m];
+    }
+    __syncthreads();
+    rows = fft_tile<+1, false>(rows, rows + nc * pitch, pl, nc, 1, pitch, tw);
+    const int64_t S = fp.a * (nc - 1) + fp.Lg;
+    const int64_t ov = fp.Lg > fp.a ? fp.Lg - fp.a : 0;
+    const int64_t lstart = fp.a * n0 - fp.center;
+    const int64_t LM = fp.lam2 * fp.M;
+    C* seamL = seams + (b * nchunks + chunk) * 2 * ov;
+    C* seamR = seamL + ov;
+    for (int64_t t = threadIdx.x; t < S; t += blockDim.x) {
+        const int64_t l = posmod(lstart + t, fp.L);
+        const int64_t km = l % fp.M;
+        C acc = mk((T)0, (T)0);
+        // columns r with 0 <= t - a r < Lg
+        int64_t rlo = t - fp.Lg + 1 <= 0 ? 0 : (t - fp.Lg + fp.a) / fp.a;
+        int64_t rhi = min((int64_t)nc - 1, t / fp.a);
+        for (int64_t r = rlo; r <= rhi; ++r) {
+            const int64_t tap = t - fp.a * r;
+            const int64_t n = n0 + r;
+            const int64_t wn = (n * fp.lam1) % fp.lam2;
+            C v = cmul(rows[r * pitch + km], __ldg(fp.taps + tap));
+            if (wn) v = cmul(v, fp.cisLM((int64_t)mulmod((uint64_t)(l % LM), (uint64_t)wn, (uint64_t)LM)));
+            acc = cadd(acc, v);
+        }
+        if (t < ov) seamL[t] = acc;
+        else if (t >= S - ov) seamR[t - (S - ov)] = acc;
+        else {
+            if (f_real) reinterpret_cast<R*>(f)[b * fp.L + l] = acc.x;
+            else reinterpret_cast<C*>(f)[b * fp.L + l] = acc;
+        }
+    }
+}
+
+template <typename T>
+__global__ void fir_seams_kernel(const cplx<T>* __restrict__ seams, void* __restrict__ f, int f_real,
+                                 FirParams<cplx<T>> fp, int64_t nchunks, int64_t B) {
+    using C = cplx<T>;
+    const int64_t ov = fp.Lg - fp.a;
+    const int64_t total = B * nchunks * ov;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e % ov;
+        const int64_t chunk = (e / ov) % nchunks;
+        const int64_t b = e / (ov * nchunks);
+        const int64_t nxt = (chunk + 1) % nchunks;
+        const C r = seams[(b * nchunks + chunk) * 2 * ov + ov + t];
+        const C lft = seams[(b * nchunks + nxt) * 2 * ov + t];
+        const int64_t l = posmod(fp.a * (chunk + 1) * fp.cols - fp.center + t, fp.L);
+        const C v = cadd(r, lft);
+        if (f_real) reinterpret_cast<T*>(f)[b * fp.L + l] = v.x;
+        else reinterpret_cast<C*>(f)[b * fp.L + l] = v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
+                                 const FftRef& fm, int64_t B, cudaStream_t st) {
+    using C = cplx<T>;
+    if (fp.N % fp.cols) return cudaErrorInvalidValue;
+    if (fp.a * fp.cols < fp.Lg - fp.a) return cudaErrorInvalidValue;
+    const size_t smem = 2 * sizeof(C) * ((size_t)fp.cols * (fp.M + 1));
+    if (smem > kSmemBudget) return cudaErrorInvalidValue;
+    auto k = fir_synthesis_kernel<T>;
+    cudaError_t e = prep_smem2(k, smem);
+    if (e != cudaSuccess) return e;
+    const int thr = threads_for(fp.cols * fp.M);
+    const int64_t nchunks = fp.N / fp.cols;
+    dim3 grid((unsigned)nchunks, (unsigned)B);
+    k<<<grid, thr, smem, st>>>(c, f, f_real, seams, fp, fm.pl, (const C*)fm.tw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (fp.Lg > fp.a) {
+        const int64_t total = B * nchunks * (fp.Lg - fp.a);
+        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        fir_seams_kernel<T><<<blocks, 256, 0, st>>>(seams, f, f_real, fp, nchunks, B);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// =====================================================================================
+// window set-up helpers
+// =====================================================================================
+// g_j(l) = exp(2 pi i sigma_j l / L) g(l - j a)   (Prop. mw_frop: g_j = M_{sigma_j} T_{ja} g)
+template <typename T>
+__global__ void coset_windows_kernel(const cplx<T>* __restrict__ g, cplx<T>* __restrict__ gj, int64_t L, int64_t a,
+                                     int64_t J, const int64_t* __restrict__ sigma, CisTable<cplx<T>> cisL) {
+    const int64_t total = J * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / L, l = e % L;
+        const int64_t src = posmod(l - j * a, L);
+        const int64_t ex = (int64_t)mulmod((uint64_t)l, (uint64_t)sigma[j], (uint64_t)L);
+        gj[e] = cmul(g[src], cisL(ex));
+    }
+}
+
+template <typename T>
+cudaError_t launch_coset_windows(const cplx<T>* g, cplx<T>* gj, int64_t L, int64_t a, int64_t J, const int64_t* sigma,
+                                 const CisTable<cplx<T>>& cisL, cudaStream_t st) {
+    const int64_t total = J * L;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    coset_windows_kernel<T><<<blocks, 256, 0, st>>>(g, gj, L, a, J, sigma, cisL);
+    return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const void* __restrict__ in, int in_real, cplx<Tout>* __restrict__ out, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        if (in_real) out[e] = mk((Tout)reinterpret_cast<const Tin*>(in)[e], (Tout)0);
+        else {
+            const cplx<Tin> v = reinterpret_cast<const cplx<Tin>*>(in)[e];
+            out[e] = mk((Tout)v.x, (Tout)v.y);
+        }
+    }
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const void* in, int in_real, cplx<Tout>* out, int64_t n, cudaStream_t st) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    convert_kernel<Tin, Tout><<<blocks, 256, 0, st>>>(in, in_real, out, n);
+    return cudaGetLastError();
+}
+
+// grad_g(y) = sum_j exp(-2 pi i sigma_j (y + j a) / L) W_j(y + j a): adjoint of g -> g_j
+template <typename T>
+__global__ void grad_combine_kernel(const cplx<T>* __restrict__ wj, void* __restrict__ grad, int grad_real, int64_t L,
+                                    int64_t a, int64_t J, const int64_t* __restrict__ sigma, CisTable<cplx<T>> cisL) {
+    using C = cplx<T>;
+    for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < L; y += (int64_t)gridDim.x * blockDim.x) {
+        C acc = mk((T)0, (T)0);
+        for (int64_t j = 0; j < J; ++j) {
+            const int64_t x = (y + j * a) % L;
+            const int64_t ex = (int64_t)mulmod((uint64_t)x, (uint64_t)sigma[j], (uint64_t)L);
+            acc = cadd(acc, cmul(wj[j * L + x], cisL(-ex)));
+        }
+        if (grad_real) reinterpret_cast<T*>(grad)[y] = acc.x;
+        else reinterpret_cast<C*>(grad)[y] = acc;
+    }
+}
+
+template <typename T>
+cudaError_t launch_grad_window_combine(const cplx<T>* wj, void* grad, int grad_real, int64_t L, int64_t a, int64_t J,
+                                       const int64_t* sigma, const CisTable<cplx<T>>& cisL, cudaStream_t st) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((L + 255) / 256, 152 * 32);
+    grad_combine_kernel<T><<<blocks, 256, 0, st>>>(wj, grad, grad_real, L, a, J, sigma, cisL);
+    return cudaGetLastError();
+}
+
+// u = 2 c / (|c|^2 + eps) (gradient of sum log(|c|^2 + eps) in the d/dRe + i d/dIm
+// convention) and per-block partial sums of log(|c|^2 + eps), for B signals of n coefficients.
+template <typename T>
+__global__ void logmag_kernel(const cplx<T>* __restrict__ c, cplx<T>* __restrict__ u, double* __restrict__ partial,
+                              int64_t n, T eps) {
+    __shared__ double red[256];
+    const int64_t b = blockIdx.y;
+    double acc = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const cplx<T> v = c[b * n + e];
+        const T m2 = v.x * v.x + v.y * v.y + eps;
+        acc += log((double)m2);
+        if (u) u[b * n + e] = cscale(v, (T)2 / m2);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[b * gridDim.x + blockIdx.x] = red[0];
+}
+
+template <typename T>
+cudaError_t launch_logmag(const cplx<T>* c, cplx<T>* u, double* partial, int64_t n, T eps, int64_t B,
+                          cudaStream_t st) {
+    dim3 grid(64, (unsigned)B);
+    logmag_kernel<T><<<grid, 256, 0, st>>>(c, u, partial, n, eps);
+    return cudaGetLastError();
+}
+
+// =====================================================================================
+// Gram blocks (float64).  For the separable lattice (at, M) of the coset decomposition and
+// every (xi, k < M):  Phi_j[i][w] = ZG~_j[xi][k + iM - at w] (i < p, w < q),
+// G = M sum_j Phi_j Phi_j^H (p x p), right-hand side ZG_0[xi][k + iM].
+// dual:  Zgamma = G^{-1} rhs ;  tight: Zgamma = G^{-1/2} rhs.
+// =====================================================================================
+constexpr int kPMax = 8;
+
+__device__ void herm_jacobi(double2 (&A)[kPMax][kPMax], double2 (&V)[kPMax][kPMax], int p) {
+    // cyclic Jacobi for a Hermitian p x p matrix: A <- V^H A V diagonal, V unitary
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j) V[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) {
+                const double m = A[i][j].x * A[i][j].x + A[i][j].y * A[i][j].y;
+                tot += m;
+                if (i != j) off += m;
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int pp = 0; pp < p - 1; ++pp)
+            for (int q = pp + 1; q < p; ++q) {
+                const double2 apq = A[pp][q];
+                const double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
+                if (mag < 1e-300) continue;
+                const double2 ph = make_double2(apq.x / mag, apq.y / mag);     // e^{i phi}
+                const double app = A[pp][pp].x, aqq = A[q][q].x;
+                const double theta = 0.5 * atan2(2 * mag, aqq - app);
+                const double cs = cos(theta), sn = sin(theta);
+                // rotation acting on columns pp, q:  [c, s e^{i phi}; -s e^{-i phi}, c]
+                for (int k = 0; k < p; ++k) {
+                    const double2 akp = A[k][pp], akq = A[k][q];
+                    // A[:,pp] = c akp - s e^{-i phi} akq ; A[:,q] = s e^{i phi} akp + c akq
+                    const double2 t1 = cmulc(akq, ph);
+                    const double2 t2 = cmul(akp, ph);
+                    A[k][pp] = make_double2(cs * akp.x - sn * t1.x, cs * akp.y - sn * t1.y);
+                    A[k][q] = make_double2(sn * t2.x + cs * akq.x, sn * t2.y + cs * akq.y);
+                    const double2 vkp = V[k][pp], vkq = V[k][q];
+                    const double2 u1 = cmulc(vkq, ph);
+                    const double2 u2 = cmul(vkp, ph);
+                    V[k][pp] = make_double2(cs * vkp.x - sn * u1.x, cs * vkp.y - sn * u1.y);
+                    V[k][q] = make_double2(sn * u2.x + cs * vkq.x, sn * u2.y + cs * vkq.y);
+                }
+                for (int k = 0; k < p; ++k) {
+                    const double2 apk = A[pp][k], aqk = A[q][k];
+                    // rows: A[pp,:] = c apk - s e^{i phi} aqk ; A[q,:] = s e^{-i phi} apk + c aqk
+                    const double2 t1 = cmul(aqk, ph);
+                    const double2 t2 = cmulc(apk, ph);
+                    A[pp][k] = make_double2(cs * apk.x - sn * t1.x, cs * apk.y - sn * t1.y);
+                    A[q][k] = make_double2(sn * t2.x + cs * aqk.x, sn * t2.y + cs * aqk.y);
+                }
+            }
+    }
+}
+
+__global__ void gram_solve_kernel(const double2* __restrict__ zg, int64_t J, double2* __restrict__ zout, SepGeom g,
+                                  int tight, int* __restrict__ status) {
+    const int64_t total = g.d * g.M;
+    const double2* ZG0 = zg;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t xi = e / g.M, k = e % g.M;
+        const int p = (int)g.p;
+        const double2 unwrap = make_double2(cospi(-2.0 * (double)xi / (double)g.d), sinpi(-2.0 * (double)xi / (double)g.d));
+        double2 G[kPMax][kPMax];
+        for (int i = 0; i < p; ++i)
+            for (int i2 = 0; i2 < p; ++i2) G[i][i2] = make_double2(0, 0);
+        for (int64_t j = 0; j < J; ++j) {
+            const double2* Z = zg + j * g.L;
+            for (int64_t w = 0; w < g.q; ++w) {
+                double2 phi[kPMax];
+                for (int i = 0; i < p; ++i) {
+                    int64_t col = k + i * g.M - g.a * w;
+                    const bool wrap = col < 0;
+                    if (wrap) col += g.K0;
+                    double2 v = Z[xi * g.K0 + col];
+                    if (wrap) v = cmul(v, unwrap);
+                    phi[i] = v;
+                }
+                for (int i = 0; i < p; ++i)
+                    for (int i2 = 0; i2 < p; ++i2) G[i][i2] = cadd(G[i][i2], cmulc(phi[i], phi[i2]));
+            }
+        }
+        const double Md = (double)g.M;
+        double2 rhs[kPMax], x[kPMax];
+        for (int i = 0; i < p; ++i) rhs[i] = ZG0[xi * g.K0 + k + i * g.M];
+        for (int i = 0; i < p; ++i)
+            for (int i2 = 0; i2 < p; ++i2) G[i][i2] = cscale(G[i][i2], Md);
+        if (p == 1) {
+            const double gv = G[0][0].x;
+            if (!(gv > 0)) atomicExch(status, 1);
+            x[0] = cscale(rhs[0], tight ? 1.0 / sqrt(gv) : 1.0 / gv);
+        } else if (!tight) {
+            // Gaussian elimination with partial pivoting
+            double2 A[kPMax][kPMax];
+            for (int i = 0; i < p; ++i) {
+                for (int i2 = 0; i2 < p; ++i2) A[i][i2] = G[i][i2];
+                x[i] = rhs[i];
+            }
+            double dmax = 0;
+            for (int i = 0; i < p; ++i) dmax = fmax(dmax, A[i][i].x);
+            for (int col = 0; col < p; ++col) {
+                int piv = col;
+                double best = 0;
+                for (int r = col; r < p; ++r) {
+                    const double m = hypot(A[r][col].x, A[r][col].y);
+                    if (m > best) { best = m; piv = r; }
+                }
+                if (!(best > 1e-14 * dmax)) { atomicExch(status, 1); best = 1; }
+                if (piv != col) {
+                    for (int i2 = 0; i2 < p; ++i2) { double2 t = A[col][i2]; A[col][i2] = A[piv][i2]; A[piv][i2] = t; }
+                    double2 t = x[col]; x[col] = x[piv]; x[piv] = t;
+                }
+                const double2 pv = A[col][col];
+                const double den = pv.x * pv.x + pv.y * pv.y;
+                const double2 inv = den > 0 ? make_double2(pv.x / den, -pv.y / den) : make_double2(0, 0);
+                for (int r = 0; r < p; ++r) {
+                    if (r == col) continue;
+                    const double2 fct = cmul(A[r][col], inv);
+                    for (int i2 = col; i2 < p; ++i2) A[r][i2] = csub(A[r][i2], cmul(fct, A[col][i2]));
+                    x[r] = csub(x[r], cmul(fct, x[col]));
+                }
+            }
+            for (int i = 0; i < p; ++i) {
+                const double2 pv = A[i][i];
+                const double den = pv.x * pv.x + pv.y * pv.y;
+                x[i] = den > 0 ? cmul(x[i], make_double2(pv.x / den, -pv.y / den)) : make_double2(0, 0);
+            }
+        } else {
+            double2 V[kPMax][kPMax];
+            herm_jacobi(G, V, p);
+            double lmax = 0;
+            for (int i = 0; i < p; ++i) lmax = fmax(lmax, G[i][i].x);
+            double2 tmp[kPMax];
+            for (int i = 0; i < p; ++i) {      // tmp = V^H rhs / sqrt(lambda)
+                double2 s = make_double2(0, 0);
+                for (int r = 0; r < p; ++r) s = cadd(s, cmulc(rhs[r], V[r][i]));
+                const double lam = G[i][i].x;
+                if (!(lam > 1e-14 * lmax)) { atomicExch(status, 1); }
+                tmp[i] = lam > 0 ? cscale(s, 1.0 / sqrt(lam)) : make_double2(0, 0);
+            }
+            for (int r = 0; r < p; ++r) {
+                double2 s = make_double2(0, 0);
+                for (int i = 0; i < p; ++i) s = cadd(s, cmul(V[r][i], tmp[i]));
+                x[r] = s;
+            }
+        }
+        for (int i = 0; i < p; ++i) zout[xi * g.K0 + k + i * g.M] = x[i];
+    }
+}
+
+cudaError_t launch_gram_solve(const double2* zg, int64_t J, double2* zout, const SepGeom& g, int tight, int* status,
+                              cudaStream_t st) {
+    if (g.p > kPMax) return cudaErrorInvalidValue;
+    const int64_t total = g.d * g.M;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 16);
+    gram_solve_kernel<<<blocks, 128, 0, st>>>(zg, J, zout, g, tight, status);
+    return cudaGetLastError();
+}
+
+// gamma(x) = g(x) / (M sum_{x' = x mod a} |g(x')|^2)  (tight: square root of the denominator);
+// exact when the window support is at most M long.
+__global__ void fir_dual_kernel(const double2* __restrict__ taps, double2* __restrict__ out, int64_t Lg, int64_t a,
+                                int64_t M, int tight, int* __restrict__ status) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Lg; t += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int64_t u = t % a; u < Lg; u += a) s += taps[u].x * taps[u].x + taps[u].y * taps[u].y;
+        s *= (double)M;
+        if (!(s > 0)) {
+            // a sample no window translate reaches: no frame
+            atomicExch(status, 1);
+            out[t] = make_double2(0, 0);
+            continue;
+        }
+        out[t] = cscale(taps[t], tight ? 1.0 / sqrt(s) : 1.0 / s);
+    }
+}
+
+cudaError_t launch_fir_dual(const double2* taps, double2* out, int64_t Lg, int64_t a, int64_t M, int tight, int* status,
+                            cudaStream_t st) {
+    fir_dual_kernel<<<(unsigned)std::min<int64_t>((Lg + 255) / 256, 1024), 256, 0, st>>>(taps, out, Lg, a, M, tight,
+                                                                                         status);
+    return cudaGetLastError();
+}
+
+#define DGT_INST_AUX(T)                                                                                               \
+    template cudaError_t launch_fir_analysis<T>(const void*, int, cplx<T>*, const FirParams<cplx<T>>&, const FftRef&, \
+                                                int64_t, cudaStream_t);                                               \
+    template cudaError_t launch_fir_synthesis<T>(const cplx<T>*, void*, int, cplx<T>*, const FirParams<cplx<T>>&,     \
+                                                 const FftRef&, int64_t, cudaStream_t);                               \
+    template cudaError_t launch_coset_windows<T>(const cplx<T>*, cplx<T>*, int64_t, int64_t, int64_t,                 \
+                                                 const int64_t*, const CisTable<cplx<T>>&, cudaStream_t);             \
+    template cudaError_t launch_grad_window_combine<T>(const cplx<T>*, void*, int, int64_t, int64_t, int64_t,         \
+                                                       const int64_t*, const CisTable<cplx<T>>&, cudaStream_t);       \
+    template cudaError_t launch_logmag<T>(const cplx<T>*, cplx<T>*, double*, int64_t, T, int64_t, cudaStream_t);
+
+DGT_INST_AUX(float)
+DGT_INST_AUX(double)
+template cudaError_t launch_convert<double, float>(const void*, int, cplx<float>*, int64_t, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const void*, int, cplx<double>*, int64_t, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const void*, int, cplx<double>*, int64_t, cudaStream_t);
+template cudaError_t launch_convert<float, float>(const void*, int, cplx<float>*, int64_t, cudaStream_t);
+
+}  // namespace dgt

@@ -1,0 +1,994 @@
+// Host side of the library: lattice algebra, route selection, tables, device buffers, the
+// orchestration of the kernels, and the extern "C" entry points declared in include/dgt.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dgt.h"
+#include "engine.h"
+
+using namespace dgt;
+
+// ---------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+#define CUDA_TRY(...)                                                                                 \
+    do {                                                                                              \
+        cudaError_t _e = (__VA_ARGS__);                                                                      \
+        if (_e != cudaSuccess) {                                                                      \
+            if (_e == cudaErrorMemoryAllocation) return fail(DGT_ERR_OOM, "%s: %s", #__VA_ARGS__, cudaGetErrorString(_e)); \
+            return fail(DGT_ERR_CUDA, "%s: %s (%s:%d)", #__VA_ARGS__, cudaGetErrorString(_e), __FILE__, __LINE__);      \
+        }                                                                                             \
+    } while (0)
+
+#define DGT_TRY(...)               \
+    do {                           \
+        int _s = (__VA_ARGS__);           \
+        if (_s != DGT_OK) return _s; \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------
+// integer lattice algebra (exact, int64)
+// ---------------------------------------------------------------------------------------
+static int64_t igcd(int64_t x, int64_t y) {
+    x = x < 0 ? -x : x;
+    y = y < 0 ? -y : y;
+    while (y) {
+        int64_t t = x % y;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+static int64_t ilcm(int64_t x, int64_t y) { return x / igcd(x, y) * y; }
+static int64_t pmod(int64_t x, int64_t m) {
+    int64_t r = x % m;
+    return r < 0 ? r + m : r;
+}
+// returns g = gcd(x, y) >= 0 and u, v with u x + v y = g
+static int64_t egcd(int64_t x, int64_t y, int64_t& u, int64_t& v) {
+    int64_t r0 = x, r1 = y, u0 = 1, u1 = 0, v0 = 0, v1 = 1;
+    while (r1 != 0) {
+        const int64_t qq = r0 / r1;
+        int64_t t = r0 - qq * r1; r0 = r1; r1 = t;
+        t = u0 - qq * u1; u0 = u1; u1 = t;
+        t = v0 - qq * v1; v0 = v1; v1 = t;
+    }
+    if (r0 < 0) { r0 = -r0; u0 = -u0; v0 = -v0; }
+    u = u0;
+    v = v0;
+    return r0;
+}
+// smallest x >= 0 with A x = B (mod m), or -1
+static int64_t solve_congruence(int64_t A, int64_t B, int64_t m) {
+    A = pmod(A, m);
+    B = pmod(B, m);
+    int64_t u, v;
+    const int64_t g = egcd(A, m, u, v);
+    if (B % g) return -1;
+    const int64_t m2 = m / g;
+    if (m2 == 1) return 0;
+    const __int128 x = (__int128)(B / g) * (__int128)pmod(u, m2);
+    return (int64_t)(x % m2);
+}
+
+struct ShearSel {
+    int64_t s0, s1, b_r;
+};
+
+// Shear parameters with U_{s0,s1}^{-1} A separable (Theorem shearform).  A time shear alone
+// (s0 = 0) works iff  s + k b = 0 (mod a)  has a solution k (proof of Prop. noshearlength):
+// then s1 = -(s + k b)/a and the separable lattice is (a, b).  Otherwise the smallest s1 >= 0
+// is taken for which eq. (modcond)  s0 X + a k1 = 0 (mod a b / X)  is solvable, with
+// X = gcd(s1 a + s, b) = k1 (s1 a + s) + k2 b; the separable lattice is diag(a b / X, X).
+static bool shear_select(int64_t L, int64_t a, int64_t b, int64_t s, ShearSel& out) {
+    if (s == 0) {
+        out = {0, 0, b};
+        return true;
+    }
+    const int64_t k = solve_congruence(b, -s, a);
+    if (k >= 0) {
+        const int64_t num = s + k * b;          // divisible by a
+        out = {0, pmod(-(num / a), L), b};
+        return true;
+    }
+    for (int64_t s1 = 0; s1 < L; ++s1) {
+        int64_t k1, k2;
+        const int64_t X = egcd(s1 * a + s, b, k1, k2);
+        const int64_t mod = a * b / X;
+        const int64_t s0 = solve_congruence(X, -a * k1, mod);
+        if (s0 >= 0) {
+            out = {pmod(s0, L), s1, X};
+            return true;
+        }
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------------------
+// FFT plans and phase tables
+// ---------------------------------------------------------------------------------------
+static bool radix_plan(int64_t n, FftPlanDev& pl) {
+    pl.n = (int)n;
+    pl.nst = 0;
+    int e2 = 0;
+    int64_t m = n;
+    while (m % 2 == 0) { m /= 2; ++e2; }
+    std::vector<int> r;
+    while (e2 >= 4 && e2 != 5) { r.push_back(16); e2 -= 4; }
+    if (e2 == 5) { r.push_back(8); r.push_back(4); }
+    else if (e2 == 3) r.push_back(8);
+    else if (e2 == 2) r.push_back(4);
+    else if (e2 == 1) r.push_back(2);
+    for (int p : {3, 5, 7})
+        while (m % p == 0) { r.push_back(p); m /= p; }
+    if (m != 1 || (int)r.size() > kMaxStages) return false;
+    for (size_t i = 0; i < r.size(); ++i) pl.R[i] = r[i];
+    pl.nst = (int)r.size();
+    return true;
+}
+
+// exp(2 pi i num / den) in double, reduced to an angle of modulus <= pi
+static void cis_host(int64_t num, int64_t den, double& c, double& s) {
+    int64_t r = pmod(num, den);
+    if (2 * r > den) r -= den;
+    const double ang = 2.0 * M_PI * (double)r / (double)den;
+    c = std::cos(ang);
+    s = std::sin(ang);
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { if (p) cudaFree(p); }
+    int alloc(size_t n) {
+        if (n <= bytes && p) return DGT_OK;
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        if (n == 0) return DGT_OK;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(DGT_ERR_OOM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+        }
+        bytes = n;
+        return DGT_OK;
+    }
+};
+
+template <typename T> static int upload_cplx(DevBuf& buf, const std::vector<double>& re_im, cudaStream_t st) {
+    const size_t n = re_im.size() / 2;
+    std::vector<T> h(2 * n);
+    for (size_t i = 0; i < 2 * n; ++i) h[i] = (T)re_im[i];
+    DGT_TRY(buf.alloc(sizeof(T) * 2 * n));
+    CUDA_TRY(cudaMemcpyAsync(buf.p, h.data(), sizeof(T) * 2 * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return DGT_OK;
+}
+
+template <typename T> struct TwTable {
+    FftRef ref;
+    DevBuf buf;
+};
+
+template <typename T> struct CisBuf {
+    DevBuf hi, lo;
+    CisTable<cplx<T>> tab;
+};
+
+template <typename T> static int make_cis(CisBuf<T>& cb, int64_t den, cudaStream_t st) {
+    int64_t S = (int64_t)std::ceil(std::sqrt((double)den));
+    if (S < 1) S = 1;
+    const int64_t nhi = den / S + 1;
+    std::vector<double> hi(2 * nhi), lo(2 * S);
+    for (int64_t k = 0; k < nhi; ++k) cis_host(k * S, den, hi[2 * k], hi[2 * k + 1]);
+    for (int64_t r = 0; r < S; ++r) cis_host(r, den, lo[2 * r], lo[2 * r + 1]);
+    DGT_TRY(upload_cplx<T>(cb.hi, hi, st));
+    DGT_TRY(upload_cplx<T>(cb.lo, lo, st));
+    cb.tab.hi = (const cplx<T>*)cb.hi.p;
+    cb.tab.lo = (const cplx<T>*)cb.lo.p;
+    cb.tab.den = den;
+    cb.tab.S = S;
+    return DGT_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------------------
+struct PlanCore {
+    int64_t L, a, M, lam1, lam2, b, N, s;
+    int route, precision;
+    int win_kind;
+    int64_t Lg, center;
+    int win_real;
+    ShearSel sh{0, 0, 0};
+    bool freq_shear = false;
+    SepGeom sep{};
+    int64_t J = 1;
+    // Algorithm 1 constants (frequency-shear branch)
+    int64_t ar = 0, Mr = 0, Nr = 0, C1 = 0, C2 = 0, C3m = 0, C4m = 0, C5m = 0, C6 = 0;
+    int64_t L1 = 0, L2 = 0;            // FFT_L split
+    int64_t fir_cols = 0;
+    std::vector<double> g_host;        // window as given (complex interleaved, float64)
+    SepGeom coset_sep{};               // (lam2 a, M): used by the dual / tight Gram blocks
+};
+
+struct dgt_plan_s {
+    virtual ~dgt_plan_s() = default;
+    PlanCore core;
+    virtual int exec(const void* f, int f_real, void* c, int64_t B, void* ws, cudaStream_t st) = 0;
+    virtual int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* ws, cudaStream_t st) = 0;
+    virtual int window_out(int which, void* out, cudaStream_t st) = 0;
+    virtual int set_window(const void* g, int is_real, cudaStream_t st) = 0;
+    virtual int grad_window(const void* f, int f_real, const void* G, void* grad, int grad_real, int64_t B,
+                            cudaStream_t st) = 0;
+    virtual int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) = 0;
+    virtual size_t ws_bytes(int64_t B) const = 0;
+    virtual size_t owned_bytes() const = 0;
+};
+
+template <typename T> struct PlanImpl final : dgt_plan_s {
+    using C = cplx<T>;
+    std::map<int64_t, std::unique_ptr<TwTable<T>>> tw;      // FFT length -> table
+    CisBuf<T> cisL, cis2L, cis2N, cisLM;
+    DevBuf sigma;                      // coset shifts (int64, J)
+    DevBuf g64;                        // window, float64 complex (L, or Lg taps for FIR)
+    DevBuf gT;                         // window in T (L or Lg)
+    DevBuf zg[3];                      // window factors: 0 analysis/adjoint, 1 dual, 2 tight
+    bool zg_ok[3] = {false, false, false};
+    DevBuf gam[3];                     // gamma in T (full length L, or Lg taps for FIR)
+    DevBuf work;                       // plan-owned workspace
+    DevBuf tmpwin;                     // scratch for window set-up
+    DevBuf status;                     // int flag for the Gram solve
+    DevBuf lossparts;
+
+    const FftRef* fft(int64_t n) {
+        auto it = tw.find(n);
+        return it == tw.end() ? nullptr : &it->second->ref;
+    }
+    int add_fft(int64_t n, cudaStream_t st) {
+        if (tw.count(n)) return DGT_OK;
+        auto t = std::make_unique<TwTable<T>>();
+        if (!radix_plan(n, t->ref.pl))
+            return fail(DGT_ERR_UNSUPPORTED, "FFT length %lld has a prime factor above 7", (long long)n);
+        if (n + 1 > tile_cap<T>())
+            return fail(DGT_ERR_UNSUPPORTED, "FFT length %lld exceeds the shared-memory tile (%lld)", (long long)n,
+                        (long long)tile_cap<T>());
+        std::vector<double> h(2 * n);
+        for (int64_t e = 0; e < n; ++e) cis_host(-e, n, h[2 * e], h[2 * e + 1]);
+        DGT_TRY(upload_cplx<T>(t->buf, h, st));
+        t->ref.tw = t->buf.p;
+        tw[n] = std::move(t);
+        return DGT_OK;
+    }
+
+    // ---- workspace layout -----------------------------------------------------------
+    struct Layout {
+        size_t zf, y, tmp, fh, seams, total;
+    };
+    static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+    Layout layout(int64_t B) const {
+        const PlanCore& k = core;
+        Layout ly{};
+        size_t off = 0;
+        if (k.route == DGT_ROUTE_FIR) {
+            FirParams<C> fp{};
+            fp.N = k.N; fp.cols = k.fir_cols; fp.Lg = k.Lg; fp.a = k.a;
+            ly.seams = off;
+            off += al(sizeof(C) * (size_t)B * fir_seam_elems(fp));
+            ly.total = off;
+            return ly;
+        }
+        ly.zf = off;
+        off += al(sizeof(C) * (size_t)B * k.L);
+        ly.y = off;
+        off += al(sizeof(C) * (size_t)B * k.J * k.sep.d * k.sep.q * k.sep.M);
+        if (k.freq_shear) {
+            ly.tmp = off;
+            off += al(sizeof(C) * (size_t)B * k.L);
+            ly.fh = off;
+            off += al(sizeof(C) * (size_t)B * k.L);
+        }
+        ly.total = off;
+        return ly;
+    }
+    size_t ws_bytes(int64_t B) const override { return layout(B).total; }
+    size_t owned_bytes() const override {
+        size_t s = sigma.bytes + g64.bytes + gT.bytes + work.bytes + tmpwin.bytes + status.bytes + lossparts.bytes;
+        for (int i = 0; i < 3; ++i) s += zg[i].bytes + gam[i].bytes;
+        for (auto& kv : tw) s += kv.second->buf.bytes;
+        s += cisL.hi.bytes + cisL.lo.bytes + cis2L.hi.bytes + cis2L.lo.bytes + cis2N.hi.bytes + cis2N.lo.bytes +
+             cisLM.hi.bytes + cisLM.lo.bytes;
+        return s;
+    }
+
+    ChirpParams<C> chirp(int64_t s, int conj) const {
+        ChirpParams<C> cp{};
+        cp.mode = pmod(s, 2 * core.L) == 0 ? PRE_NONE : PRE_CHIRP;
+        cp.L = core.L;
+        cp.s_2L = pmod(s, 2 * core.L);
+        cp.conj = conj;
+        cp.cis2L = cis2L.tab;
+        return cp;
+    }
+    ChirpParams<C> nochirp() const {
+        ChirpParams<C> cp{};
+        cp.mode = PRE_NONE;
+        cp.L = core.L;
+        cp.cis2L = cis2L.tab;
+        return cp;
+    }
+
+    PostParams<C> post() const {
+        const PlanCore& k = core;
+        PostParams<C> pp{};
+        pp.L = k.L; pp.M = k.M; pp.N = k.N; pp.b = k.b; pp.a = k.a;
+        pp.cisL = cisL.tab;
+        pp.cis2N = cis2N.tab;
+        if (k.route == DGT_ROUTE_COSET) {
+            pp.mode = POST_COSET;
+            pp.lam2 = k.lam2;
+            pp.at = k.lam2 * k.a;
+            pp.sigma = (const int64_t*)sigma.p;
+        } else if (!k.freq_shear) {
+            pp.mode = POST_SHEAR0;
+            pp.s1a_modL = (int64_t)(((__int128)k.sh.s1 * k.a) % k.L);
+            pp.C1_2N = (int64_t)(((__int128)k.sh.s1 * k.a % (2 * k.N)) * ((k.L + 1) % (2 * k.N)) % (2 * k.N));
+        } else {
+            const int64_t twoN = 2 * k.N;
+            pp.mode = POST_SHEAR1;
+            pp.Nr = k.Nr;
+            pp.C1 = k.C1;
+            pp.C2_N = pmod(k.C2, k.N);
+            pp.C1_2N_ = pmod(k.C1, twoN);
+            pp.C2_2N = pmod(k.C2, twoN);
+            pp.C3_2N = k.C3m;
+            pp.C4_2N = k.C4m;
+            pp.C5_2N = k.C5m;
+            pp.s1ar_L = pmod(-(int64_t)(((__int128)k.sh.s1 * k.ar) % k.L), k.L);
+            pp.C6_L = pmod(k.C6, k.L);
+        }
+        return pp;
+    }
+
+    // ---- set-up -----------------------------------------------------------------------
+    int init(cudaStream_t st) {
+        PlanCore& k = core;
+        DGT_TRY(make_cis(cisL, k.L, st));
+        DGT_TRY(make_cis(cis2L, 2 * k.L, st));
+        DGT_TRY(make_cis(cis2N, 2 * k.N, st));
+        DGT_TRY(make_cis(cisLM, k.lam2 * k.M, st));
+        // coset shifts sigma_j = j s mod b (Prop. mwindec)
+        std::vector<int64_t> sg(k.lam2);
+        for (int64_t j = 0; j < k.lam2; ++j) sg[j] = (j * k.s) % k.b;
+        DGT_TRY(sigma.alloc(sizeof(int64_t) * k.lam2));
+        CUDA_TRY(cudaMemcpyAsync(sigma.p, sg.data(), sizeof(int64_t) * k.lam2, cudaMemcpyHostToDevice, st));
+        DGT_TRY(status.alloc(sizeof(int)));
+        // FFT tables
+        if (k.route == DGT_ROUTE_FIR) {
+            DGT_TRY(add_fft(k.M, st));
+        } else {
+            DGT_TRY(add_fft(k.sep.d, st));
+            DGT_TRY(add_fft(k.sep.M, st));
+            if (k.freq_shear) {
+                DGT_TRY(add_fft(k.L1, st));
+                DGT_TRY(add_fft(k.L2, st));
+            }
+        }
+        // coset Gram lattice tables (dual / tight)
+        DGT_TRY(add_fft_if_ok(k.coset_sep.d, st));
+        // upload the window (float64)
+        const int64_t n = (int64_t)k.g_host.size() / 2;
+        std::vector<double> gh = k.g_host;
+        DGT_TRY(upload_cplx<double>(g64, gh, st));
+        DGT_TRY(gT.alloc(sizeof(C) * n));
+        CUDA_TRY(launch_convert<double, T>(g64.p, 0, (C*)gT.p, n, st));
+        DGT_TRY(build_factor(0, (const C*)gT.p, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return DGT_OK;
+    }
+    int add_fft_if_ok(int64_t n, cudaStream_t st) {
+        // the dual / tight set-up is optional: failures surface when it is requested
+        FftPlanDev pl;
+        if (!radix_plan(n, pl) || n + 1 > tile_cap<T>()) return DGT_OK;
+        return add_fft(n, st);
+    }
+
+    // window factor of `gam` (device, T, full length L or FIR taps) into zg[slot]
+    int build_factor(int slot, const C* gw, cudaStream_t st) {
+        const PlanCore& k = core;
+        if (k.route == DGT_ROUTE_FIR) {
+            zg_ok[slot] = true;      // FIR route uses the taps directly
+            return DGT_OK;
+        }
+        DGT_TRY(zg[slot].alloc(sizeof(C) * (size_t)k.J * k.L));
+        C* out = (C*)zg[slot].p;
+        const FftRef* fd = fft(k.sep.d);
+        if (k.route == DGT_ROUTE_COSET) {
+            DGT_TRY(tmpwin.alloc(sizeof(C) * (size_t)k.J * k.L));
+            CUDA_TRY(launch_coset_windows<T>(gw, (C*)tmpwin.p, k.L, k.a, k.J, (const int64_t*)sigma.p, cisL.tab, st));
+            CUDA_TRY(launch_zak_fwd<T>(tmpwin.p, 0, k.L, out, k.L, k.L, k.sep.d, *fd, nochirp(), k.J, st));
+        } else if (!k.freq_shear) {
+            CUDA_TRY(launch_zak_fwd<T>(gw, 0, k.L, out, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 0), 1, st));
+        } else {
+            // g^ = pchirp(L, -s0) FFT(pchirp(L, s1) g) / L   (Algorithm 1, frequency-shear branch)
+            DGT_TRY(tmpwin.alloc(sizeof(C) * 2 * (size_t)k.L));
+            C* t1 = (C*)tmpwin.p;
+            C* t2 = t1 + k.L;
+            CUDA_TRY(launch_fftL_cols<T>(gw, 0, t1, k.L1, k.L2, -1, *fft(k.L1), chirp(k.sh.s1, 0), cisL.tab, 1, st));
+            CUDA_TRY(launch_fftL_rows<T>(t1, t2, 0, k.L1, k.L2, -1, *fft(k.L2), chirp(-k.sh.s0, 0), (T)1 / (T)k.L, 1, st));
+            CUDA_TRY(launch_zak_fwd<T>(t2, 0, k.L, out, k.L, k.L, k.sep.d, *fd, nochirp(), 1, st));
+        }
+        zg_ok[slot] = true;
+        return DGT_OK;
+    }
+
+    int set_window(const void* g, int is_real, cudaStream_t st) override {
+        const PlanCore& k = core;
+        const int64_t n = k.win_kind == DGT_WINDOW_FIR ? k.Lg : k.L;
+        CUDA_TRY(launch_convert<T, T>(g, is_real, (C*)gT.p, n, st));
+        CUDA_TRY(launch_convert<T, double>(g, is_real, (double2*)g64.p, n, st));
+        zg_ok[1] = zg_ok[2] = false;
+        return build_factor(0, (const C*)gT.p, st);
+    }
+
+    // ---- analysis ---------------------------------------------------------------------
+    int exec(const void* f, int f_real, void* c, int64_t B, void* wsp, cudaStream_t st) override {
+        const PlanCore& k = core;
+        if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+        const Layout ly = layout(B);
+        char* ws = (char*)wsp;
+        if (!ws) {
+            DGT_TRY(work.alloc(ly.total));
+            ws = (char*)work.p;
+        }
+        if (k.route == DGT_ROUTE_FIR) {
+            FirParams<C> fp = fir_params((const C*)gT.p);
+            CUDA_TRY(launch_fir_analysis<T>(f, f_real, (C*)c, fp, *fft(k.M), B, st));
+            return DGT_OK;
+        }
+        C* zf = (C*)(ws + ly.zf);
+        C* y = (C*)(ws + ly.y);
+        const FftRef* fd = fft(k.sep.d);
+        if (k.route == DGT_ROUTE_COSET) {
+            CUDA_TRY(launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, k.sep.d, *fd, nochirp(), B, st));
+        } else if (!k.freq_shear) {
+            CUDA_TRY(launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 0), B, st));
+        } else {
+            C* tmp = (C*)(ws + ly.tmp);
+            C* fh = (C*)(ws + ly.fh);
+            CUDA_TRY(launch_fftL_cols<T>(f, f_real, tmp, k.L1, k.L2, -1, *fft(k.L1), chirp(k.sh.s1, 0), cisL.tab, B, st));
+            CUDA_TRY(launch_fftL_rows<T>(tmp, fh, 0, k.L1, k.L2, -1, *fft(k.L2), chirp(-k.sh.s0, 0), (T)1, B, st));
+            CUDA_TRY(launch_zak_fwd<T>(fh, 0, k.L, zf, k.L, k.L, k.sep.d, *fd, nochirp(), B, st));
+        }
+        CUDA_TRY(launch_prod_ifft<T>(zf, (const C*)zg[0].p, k.J, y, k.sep, *fd, B, st));
+        CUDA_TRY(launch_fft_post<T>(y, (C*)c, k.sep, k.J, *fft(k.sep.M), post(), B, st));
+        return DGT_OK;
+    }
+
+    FirParams<C> fir_params(const C* taps) const {
+        const PlanCore& k = core;
+        FirParams<C> fp{};
+        fp.L = k.L; fp.a = k.a; fp.M = k.M; fp.N = k.N; fp.lam1 = k.lam1; fp.lam2 = k.lam2;
+        fp.Lg = k.Lg; fp.center = k.center; fp.taps = taps; fp.cisLM = cisLM.tab; fp.cols = k.fir_cols;
+        return fp;
+    }
+
+    // ---- synthesis ----------------------------------------------------------------------
+    int ensure_window(int which, cudaStream_t st) {
+        if (which == 0 || zg_ok[which]) return DGT_OK;
+        const PlanCore& k = core;
+        const int tight = which == 2;
+        if (k.route == DGT_ROUTE_FIR || k.win_kind == DGT_WINDOW_FIR) {
+            if (k.Lg > k.M)
+                return fail(DGT_ERR_UNSUPPORTED, "dual / tight of an FIR window longer than M is not implemented");
+        }
+        CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(int), st));
+        if (k.win_kind == DGT_WINDOW_FIR) {
+            // short window: S is diagonal; gamma has the same support
+            DevBuf g64o;
+            DGT_TRY(g64o.alloc(sizeof(double2) * k.Lg));
+            CUDA_TRY(launch_fir_dual((const double2*)g64.p, (double2*)g64o.p, k.Lg, k.a, k.M, tight, (int*)status.p, st));
+            DGT_TRY(check_status(st));
+            if (k.route == DGT_ROUTE_FIR) {
+                DGT_TRY(gam[which].alloc(sizeof(C) * k.Lg));
+                CUDA_TRY(launch_convert<double, T>(g64o.p, 0, (C*)gam[which].p, k.Lg, st));
+                zg_ok[which] = true;
+                CUDA_TRY(cudaStreamSynchronize(st));
+                return DGT_OK;
+            }
+            // Zak route with an FIR window: expand gamma to full length
+            DevBuf full;
+            DGT_TRY(full.alloc(sizeof(double2) * k.L));
+            std::vector<double> taps(2 * k.Lg);
+            CUDA_TRY(cudaMemcpyAsync(taps.data(), g64o.p, sizeof(double2) * k.Lg, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<double> fullh(2 * k.L, 0.0);
+            for (int64_t t = 0; t < k.Lg; ++t) {
+                const int64_t l = pmod(t - k.center, k.L);
+                fullh[2 * l] = taps[2 * t];
+                fullh[2 * l + 1] = taps[2 * t + 1];
+            }
+            DGT_TRY(upload_cplx<T>(gam[which], fullh, st));
+            DGT_TRY(build_factor(which, (const C*)gam[which].p, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            return DGT_OK;
+        }
+        // full window: Zak-domain Gram blocks of the coset decomposition, float64
+        const SepGeom& cg = k.coset_sep;
+        if (cg.p > 8) return fail(DGT_ERR_UNSUPPORTED, "Gram blocks of size %lld > 8", (long long)cg.p);
+        TwTable<double> twd;
+        if (!radix_plan(cg.d, twd.ref.pl) || cg.d + 1 > tile_cap<double>())
+            return fail(DGT_ERR_UNSUPPORTED, "dual window: Zak length %lld unsupported", (long long)cg.d);
+        {
+            std::vector<double> h(2 * cg.d);
+            for (int64_t e = 0; e < cg.d; ++e) cis_host(-e, cg.d, h[2 * e], h[2 * e + 1]);
+            DGT_TRY(upload_cplx<double>(twd.buf, h, st));
+            twd.ref.tw = twd.buf.p;
+        }
+        CisBuf<double> cisL64;
+        DGT_TRY(make_cis(cisL64, k.L, st));
+        DevBuf gj, zj, zo, gout;
+        DGT_TRY(gj.alloc(sizeof(double2) * (size_t)k.lam2 * k.L));
+        DGT_TRY(zj.alloc(sizeof(double2) * (size_t)k.lam2 * k.L));
+        DGT_TRY(zo.alloc(sizeof(double2) * (size_t)k.L));
+        DGT_TRY(gout.alloc(sizeof(double2) * (size_t)k.L));
+        CUDA_TRY(launch_coset_windows<double>((const double2*)g64.p, (double2*)gj.p, k.L, k.a, k.lam2,
+                                              (const int64_t*)sigma.p, cisL64.tab, st));
+        ChirpParams<double2> none{};
+        none.mode = PRE_NONE;
+        none.L = k.L;
+        CUDA_TRY(launch_zak_fwd<double>(gj.p, 0, k.L, (double2*)zj.p, k.L, k.L, cg.d, twd.ref, none, k.lam2, st));
+        CUDA_TRY(launch_gram_solve((const double2*)zj.p, k.lam2, (double2*)zo.p, cg, tight, (int*)status.p, st));
+        DGT_TRY(check_status(st));
+        CUDA_TRY(launch_zak_inv<double>((const double2*)zo.p, k.L, gout.p, 0, k.L, k.L, cg.d, twd.ref, none,
+                                        1.0 / (double)cg.d, 1, st));
+        DGT_TRY(gam[which].alloc(sizeof(C) * k.L));
+        CUDA_TRY(launch_convert<double, T>(gout.p, 0, (C*)gam[which].p, k.L, st));
+        DGT_TRY(build_factor(which, (const C*)gam[which].p, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return DGT_OK;
+    }
+    int check_status(cudaStream_t st) {
+        int h = 0;
+        CUDA_TRY(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (h) return fail(DGT_ERR_NOT_FRAME, "a Gram block is singular or ill-conditioned: no frame");
+        return DGT_OK;
+    }
+
+    int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, cudaStream_t st) override {
+        const PlanCore& k = core;
+        if (which < 0 || which > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which);
+        if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+        if (!zg_ok[which]) {
+            if (wsp) return fail(DGT_ERR_ARG, "the dual / tight window is not cached yet (call dgt_window_dual/_tight)");
+            DGT_TRY(ensure_window(which, st));
+        }
+        const Layout ly = layout(B);
+        char* ws = (char*)wsp;
+        if (!ws) {
+            DGT_TRY(work.alloc(ly.total));
+            ws = (char*)work.p;
+        }
+        if (k.route == DGT_ROUTE_FIR) {
+            const C* taps = which == 0 ? (const C*)gT.p : (const C*)gam[which].p;
+            FirParams<C> fp = fir_params(taps);
+            CUDA_TRY(launch_fir_synthesis<T>((const C*)c, f, f_real, (C*)(ws + ly.seams), fp, *fft(k.M), B, st));
+            return DGT_OK;
+        }
+        C* zf = (C*)(ws + ly.zf);
+        C* y = (C*)(ws + ly.y);
+        const FftRef* fd = fft(k.sep.d);
+        CUDA_TRY(launch_pre_ifft<T>((const C*)c, y, k.sep, k.J, *fft(k.sep.M), post(), B, st));
+        CUDA_TRY(launch_fft_prod_adj<T>(y, (const C*)zg[which].p, k.J, zf, k.sep, *fd, B, st));
+        if (k.route == DGT_ROUTE_COSET) {
+            CUDA_TRY(launch_zak_inv<T>(zf, k.L, f, f_real, k.L, k.L, k.sep.d, *fd, nochirp(), (T)1, B, st));
+        } else if (!k.freq_shear) {
+            CUDA_TRY(launch_zak_inv<T>(zf, k.L, f, f_real, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 1), (T)1, B, st));
+        } else {
+            C* tmp = (C*)(ws + ly.tmp);
+            C* fh = (C*)(ws + ly.fh);
+            CUDA_TRY(launch_zak_inv<T>(zf, k.L, fh, 0, k.L, k.L, k.sep.d, *fd, nochirp(), (T)1, B, st));
+            // adjoint of f -> pchirp(-s0) FFT(pchirp(s1) f): conj chirps, unnormalised inverse DFT
+            CUDA_TRY(launch_fftL_cols<T>(fh, 0, tmp, k.L1, k.L2, +1, *fft(k.L1), chirp(-k.sh.s0, 1), cisL.tab, B, st));
+            CUDA_TRY(launch_fftL_rows<T>(tmp, f, f_real, k.L1, k.L2, +1, *fft(k.L2), chirp(k.sh.s1, 1), (T)1, B, st));
+        }
+        return DGT_OK;
+    }
+
+    int window_out(int which, void* out, cudaStream_t st) override {
+        const PlanCore& k = core;
+        DGT_TRY(ensure_window(which, st));
+        if (k.route == DGT_ROUTE_FIR) {
+            // expand the taps to a full-length window
+            std::vector<T> taps(2 * k.Lg);
+            CUDA_TRY(cudaMemcpyAsync(taps.data(), gam[which].p, sizeof(C) * k.Lg, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<T> full(2 * k.L, (T)0);
+            for (int64_t t = 0; t < k.Lg; ++t) {
+                const int64_t l = pmod(t - k.center, k.L);
+                full[2 * l] = taps[2 * t];
+                full[2 * l + 1] = taps[2 * t + 1];
+            }
+            CUDA_TRY(cudaMemcpyAsync(out, full.data(), sizeof(C) * k.L, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            return DGT_OK;
+        }
+        CUDA_TRY(cudaMemcpyAsync(out, gam[which].p, sizeof(C) * k.L, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return DGT_OK;
+    }
+
+    // ---- gradients ------------------------------------------------------------------------
+    int grad_window(const void* f, int f_real, const void* G, void* grad, int grad_real, int64_t B,
+                    cudaStream_t st) override {
+        const PlanCore& k = core;
+        if (k.win_kind != DGT_WINDOW_FULL) return fail(DGT_ERR_UNSUPPORTED, "window gradient needs a full-length window");
+        // through the coset decomposition (any route gives the same coefficients)
+        const SepGeom& cg = k.coset_sep;
+        DGT_TRY(add_fft(cg.d, st));
+        DGT_TRY(add_fft(cg.M, st));
+        const FftRef* fd = fft(cg.d);
+        PostParams<C> pp{};
+        pp.mode = POST_COSET;
+        pp.L = k.L; pp.M = k.M; pp.N = k.N; pp.b = k.b; pp.a = k.a;
+        pp.lam2 = k.lam2; pp.at = k.lam2 * k.a; pp.sigma = (const int64_t*)sigma.p;
+        pp.cisL = cisL.tab; pp.cis2N = cis2N.tab;
+        const size_t need = al(sizeof(C) * (size_t)B * k.L) + al(sizeof(C) * (size_t)B * k.M * k.N) +
+                            2 * al(sizeof(C) * (size_t)k.lam2 * k.L);
+        DevBuf scratch;
+        DGT_TRY(scratch.alloc(need));
+        char* p = (char*)scratch.p;
+        C* zf = (C*)p; p += al(sizeof(C) * (size_t)B * k.L);
+        C* y = (C*)p; p += al(sizeof(C) * (size_t)B * k.M * k.N);
+        C* v = (C*)p; p += al(sizeof(C) * (size_t)k.lam2 * k.L);
+        C* wj = (C*)p;
+        CUDA_TRY(launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, cg.d, *fd, nochirp(), B, st));
+        CUDA_TRY(launch_pre_ifft<T>((const C*)G, y, cg, k.lam2, *fft(cg.M), pp, B, st));
+        CUDA_TRY(launch_fft_grad_window<T>(y, zf, k.lam2, v, cg, *fd, B, st));
+        CUDA_TRY(launch_zak_inv<T>(v, k.L, wj, 0, k.L, k.L, cg.d, *fd, nochirp(), (T)1, k.lam2, st));
+        CUDA_TRY(launch_grad_window_combine<T>(wj, grad, grad_real, k.L, k.a, k.lam2, (const int64_t*)sigma.p,
+                                               cisL.tab, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return DGT_OK;
+    }
+
+    int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) override {
+        const PlanCore& k = core;
+        DGT_TRY(lossparts.alloc(sizeof(double) * 64 * B));
+        CUDA_TRY(launch_logmag<T>((const C*)c, (C*)G, (double*)lossparts.p, k.M * k.N, (T)eps, B, st));
+        std::vector<double> h(64 * B);
+        CUDA_TRY(cudaMemcpyAsync(h.data(), lossparts.p, sizeof(double) * 64 * B, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<double> out(B, 0.0);
+        for (int64_t b = 0; b < B; ++b)
+            for (int i = 0; i < 64; ++i) out[b] += h[b * 64 + i];
+        CUDA_TRY(cudaMemcpyAsync(loss, out.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return DGT_OK;
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// plan creation
+// ---------------------------------------------------------------------------------------
+static SepGeom make_sep(int64_t L, int64_t a, int64_t M) {
+    SepGeom g{};
+    g.L = L; g.a = a; g.M = M; g.b = L / M; g.N = L / a;
+    g.c = igcd(a, M);
+    g.d = igcd(g.b, g.N);
+    g.p = a / g.c;
+    g.q = M / g.c;
+    g.K0 = L / g.d;
+    return g;
+}
+
+static bool fft_ok(int64_t n, int precision) {
+    FftPlanDev pl;
+    if (!radix_plan(n, pl)) return false;
+    return precision == DGT_F64 ? n + 1 <= tile_cap<double>() : n + 1 <= tile_cap<float>();
+}
+
+static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t lam1, int64_t lam2, const dgt_window* g,
+                       int route, int precision, cudaStream_t st) {
+    if (!out || !g || !g->data) return fail(DGT_ERR_ARG, "null plan or window pointer");
+    *out = nullptr;
+    if (L <= 0 || a <= 0 || M <= 0 || lam2 <= 0) return fail(DGT_ERR_ARG, "L, a, M, lambda2 must be positive");
+    if (lam1 < 0 || lam1 >= lam2 || igcd(lam1, lam2) != 1) return fail(DGT_ERR_ARG, "need 0 <= lambda1 < lambda2, gcd 1");
+    if (L > ((int64_t)1 << 30)) return fail(DGT_ERR_UNSUPPORTED, "L above 2^30");
+    if (L % a || L % M || L % (lam2 * ilcm(a, M)))
+        return fail(DGT_ERR_LENGTH, "L=%lld is not a multiple of lambda2*lcm(a,M)=%lld", (long long)L,
+                    (long long)(lam2 * ilcm(a, M)));
+    if (precision != DGT_F32 && precision != DGT_F64) return fail(DGT_ERR_ARG, "bad precision");
+    if (route < DGT_ROUTE_AUTO || route > DGT_ROUTE_FIR) return fail(DGT_ERR_ARG, "bad route");
+    if (g->kind != DGT_WINDOW_FULL && g->kind != DGT_WINDOW_FIR) return fail(DGT_ERR_ARG, "bad window kind");
+    if (g->kind == DGT_WINDOW_FULL && g->len != L) return fail(DGT_ERR_ARG, "full window needs len == L");
+    if (g->kind == DGT_WINDOW_FIR && (g->len <= 0 || g->len > L / 2 || g->center < 0 || g->center >= g->len))
+        return fail(DGT_ERR_ARG, "FIR window needs 0 < len <= L/2 and 0 <= center < len");
+
+    PlanCore k{};
+    k.L = L; k.a = a; k.M = M; k.lam1 = lam1; k.lam2 = lam2;
+    k.b = L / M; k.N = L / a; k.s = k.b * lam1 / lam2;
+    k.precision = precision;
+    k.win_kind = g->kind;
+    k.Lg = g->len;
+    k.center = g->kind == DGT_WINDOW_FIR ? g->center : 0;
+    k.win_real = g->is_real;
+    k.g_host.assign(2 * g->len, 0.0);
+    for (int64_t i = 0; i < g->len; ++i) {
+        k.g_host[2 * i] = g->is_real ? g->data[i] : g->data[2 * i];
+        k.g_host[2 * i + 1] = g->is_real ? 0.0 : g->data[2 * i + 1];
+    }
+    k.coset_sep = make_sep(L, lam2 * a, M);
+
+    // shear parameters (always computed; reported by dgt_plan_get_info)
+    if (!shear_select(L, a, k.b, k.s, k.sh)) return fail(DGT_ERR_ARG, "no shear found");
+    k.freq_shear = k.sh.s0 != 0;
+
+    if (route == DGT_ROUTE_AUTO) {
+        if (g->kind == DGT_WINDOW_FIR) route = DGT_ROUTE_FIR;
+        else route = k.freq_shear ? DGT_ROUTE_COSET : DGT_ROUTE_SHEAR;
+    }
+    if (route == DGT_ROUTE_FIR && g->kind != DGT_WINDOW_FIR)
+        return fail(DGT_ERR_ARG, "the FIR route needs an FIR window");
+    if (route != DGT_ROUTE_FIR && g->kind == DGT_WINDOW_FIR) {
+        // full-window route with a short window: expand it
+        std::vector<double> full(2 * L, 0.0);
+        for (int64_t t = 0; t < g->len; ++t) {
+            const int64_t l = pmod(t - g->center, L);
+            full[2 * l] = k.g_host[2 * t];
+            full[2 * l + 1] = k.g_host[2 * t + 1];
+        }
+        k.g_host.swap(full);
+        k.win_kind = DGT_WINDOW_FULL;
+        k.Lg = L;
+        k.center = 0;
+    }
+    k.route = route;
+    if (route != DGT_ROUTE_SHEAR) k.freq_shear = false;
+
+    if (route == DGT_ROUTE_FIR) {
+        if (!fft_ok(M, precision)) return fail(DGT_ERR_UNSUPPORTED, "FFT length M=%lld unsupported", (long long)M);
+        // columns per CTA: a divisor of N, at least ceil(Lg/a), fitting the shared-memory tile
+        const size_t csz = precision == DGT_F64 ? 16 : 8;
+        const int64_t need = std::max<int64_t>(1, (k.Lg + a - 1) / a);
+        auto fits = [&](int64_t cc) {
+            return csz * (2 * (size_t)cc * (M + 1) + (size_t)(a * (cc - 1) + k.Lg)) <= kSmemBudget;
+        };
+        int64_t best = 0;
+        for (int64_t cc = 64; cc >= 1; --cc)
+            if (k.N % cc == 0 && cc >= need && fits(cc)) { best = cc; break; }
+        if (best == 0) {
+            // analysis works with any chunking; synthesis needs the seam condition
+            for (int64_t cc = 64; cc >= 1; --cc)
+                if (k.N % cc == 0 && fits(cc)) { best = cc; break; }
+        }
+        if (best == 0) return fail(DGT_ERR_UNSUPPORTED, "FIR route: M=%lld too long for one tile", (long long)M);
+        k.fir_cols = best;
+    } else if (route == DGT_ROUTE_COSET) {
+        k.sep = make_sep(L, lam2 * a, M);
+        k.J = lam2;
+    } else if (!k.freq_shear) {
+        k.sep = make_sep(L, a, M);
+        k.J = 1;
+    } else {
+        // frequency-side shear: separable DGT with time step b_r and N_r channels on FFT(f)
+        const int64_t br = k.sh.b_r;
+        k.ar = a * k.b / br;
+        k.Mr = L / br;
+        k.Nr = L / k.ar;
+        k.C1 = k.ar / a;
+        k.C2 = -(k.sh.s0 * br) / a;
+        const int64_t twoN = 2 * k.N;
+        k.C3m = (int64_t)((__int128)pmod(a * k.sh.s1, twoN) * ((L + 1) % twoN) % twoN);
+        k.C4m = (int64_t)((__int128)pmod(k.C2 * br, twoN) * ((L + 1) % twoN) % twoN);
+        k.C5m = pmod(2 * k.C1 * br, twoN);
+        k.C6 = (int64_t)(((__int128)k.sh.s0 * k.sh.s1 + 1) * br % L);
+        k.sep = make_sep(L, br, k.Nr);
+        k.J = 1;
+        // L = L1 L2, both transformable in one tile, as balanced as possible
+        int64_t b1 = 0;
+        for (int64_t x = 1; x * x <= L; ++x)
+            if (L % x == 0 && fft_ok(x, precision) && fft_ok(L / x, precision)) b1 = x;
+        if (b1 == 0) return fail(DGT_ERR_UNSUPPORTED, "FFT_L split of L=%lld unsupported", (long long)L);
+        k.L1 = b1;
+        k.L2 = L / b1;
+    }
+    if (route != DGT_ROUTE_FIR) {
+        if (!fft_ok(k.sep.d, precision) || !fft_ok(k.sep.M, precision))
+            return fail(DGT_ERR_UNSUPPORTED, "separable FFT lengths d=%lld, M=%lld unsupported", (long long)k.sep.d,
+                        (long long)k.sep.M);
+    }
+
+    dgt_plan_s* p = nullptr;
+    int s;
+    if (precision == DGT_F32) {
+        auto* q = new PlanImpl<float>();
+        q->core = k;
+        s = q->init(st);
+        p = q;
+    } else {
+        auto* q = new PlanImpl<double>();
+        q->core = k;
+        s = q->init(st);
+        p = q;
+    }
+    if (s != DGT_OK) {
+        delete p;
+        return s;
+    }
+    *out = p;
+    return DGT_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// extern "C"
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+int dgt_plan_create(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t lambda1, int64_t lambda2,
+                    const dgt_window* g, int route, int precision, void* stream) {
+    try {
+        return create_plan(plan, L, a, M, lambda1, lambda2, g, route, precision, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fail(DGT_ERR_OOM, "host allocation failed");
+    }
+}
+
+int dgt_plan_get_info(dgt_plan_t plan, dgt_plan_info* info) {
+    if (!plan || !info) return fail(DGT_ERR_ARG, "null pointer");
+    const PlanCore& k = plan->core;
+    memset(info, 0, sizeof(*info));
+    info->L = k.L; info->a = k.a; info->M = k.M; info->lambda1 = k.lam1; info->lambda2 = k.lam2;
+    info->b = k.b; info->N = k.N; info->s = k.s;
+    info->route = k.route;
+    info->precision = k.precision;
+    info->s0 = k.sh.s0; info->s1 = k.sh.s1; info->b_r = k.sh.b_r;
+    info->sep_a = k.sep.a; info->sep_M = k.sep.M;
+    info->c = k.sep.c; info->d = k.sep.d; info->p = k.sep.p; info->q = k.sep.q;
+    info->n_windows = k.J;
+    info->fir_len = k.route == DGT_ROUTE_FIR ? k.Lg : 0;
+    return DGT_OK;
+}
+
+int dgt_plan_set_window(dgt_plan_t plan, const void* g_dev, int is_real, void* stream) {
+    if (!plan || !g_dev) return fail(DGT_ERR_ARG, "null pointer");
+    return plan->set_window(g_dev, is_real, (cudaStream_t)stream);
+}
+
+int dgt_exec(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    return plan->exec(f, f_is_real, c, batch, nullptr, (cudaStream_t)stream);
+}
+
+int idgt_exec(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    return plan->iexec(c, f, f_real_out, batch, which_window, nullptr, (cudaStream_t)stream);
+}
+
+int dgt_workspace_bytes(dgt_plan_t plan, int64_t batch, size_t* bytes) {
+    if (!plan || !bytes || batch < 0) return fail(DGT_ERR_ARG, "bad argument");
+    *bytes = plan->ws_bytes(batch);
+    return DGT_OK;
+}
+
+int dgt_exec_ws(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* workspace, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch) || (!workspace && plan->ws_bytes(batch)))
+        return fail(DGT_ERR_ARG, "null pointer");
+    if (((uintptr_t)workspace) & 255) return fail(DGT_ERR_ARG, "workspace must be 256-byte aligned");
+    return plan->exec(f, f_is_real, c, batch, workspace ? workspace : (void*)1, (cudaStream_t)stream);
+}
+
+int idgt_exec_ws(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
+                 void* workspace, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch) || (!workspace && plan->ws_bytes(batch)))
+        return fail(DGT_ERR_ARG, "null pointer");
+    if (((uintptr_t)workspace) & 255) return fail(DGT_ERR_ARG, "workspace must be 256-byte aligned");
+    return plan->iexec(c, f, f_real_out, batch, which_window, workspace ? workspace : (void*)1, (cudaStream_t)stream);
+}
+
+int dgt_window_dual(dgt_plan_t plan, void* gamma_out, void* stream) {
+    if (!plan || !gamma_out) return fail(DGT_ERR_ARG, "null pointer");
+    return plan->window_out(1, gamma_out, (cudaStream_t)stream);
+}
+
+int dgt_window_tight(dgt_plan_t plan, void* gt_out, void* stream) {
+    if (!plan || !gt_out) return fail(DGT_ERR_ARG, "null pointer");
+    return plan->window_out(2, gt_out, (cudaStream_t)stream);
+}
+
+int dgt_grad_window(dgt_plan_t plan, const void* f, int f_is_real, const void* G, void* grad_g, int grad_real,
+                    int64_t batch, void* stream) {
+    if (!plan || !f || !G || !grad_g || batch <= 0) return fail(DGT_ERR_ARG, "bad argument");
+    return plan->grad_window(f, f_is_real, G, grad_g, grad_real, batch, (cudaStream_t)stream);
+}
+
+int dgt_logmag_loss(dgt_plan_t plan, const void* c, void* G, double* loss_dev, double eps, int64_t batch, void* stream) {
+    if (!plan || !c || !loss_dev || batch <= 0) return fail(DGT_ERR_ARG, "bad argument");
+    return plan->logmag(c, G, loss_dev, eps, batch, (cudaStream_t)stream);
+}
+
+int dgt_plan_bytes(dgt_plan_t plan, size_t* bytes) {
+    if (!plan || !bytes) return fail(DGT_ERR_ARG, "null pointer");
+    *bytes = plan->owned_bytes();
+    return DGT_OK;
+}
+
+int dgt_sync(void* stream) {
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaGetLastError());
+    return DGT_OK;
+}
+
+void dgt_plan_destroy(dgt_plan_t plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    delete plan;
+}
+
+const char* dgt_strerror(int status) {
+    switch (status) {
+        case DGT_OK: return "DGT_OK";
+        case DGT_ERR_ARG: return "DGT_ERR_ARG";
+        case DGT_ERR_LENGTH: return "DGT_ERR_LENGTH";
+        case DGT_ERR_NOT_FRAME: return "DGT_ERR_NOT_FRAME";
+        case DGT_ERR_CUDA: return "DGT_ERR_CUDA";
+        case DGT_ERR_OOM: return "DGT_ERR_OOM";
+        case DGT_ERR_TIMEOUT: return "DGT_ERR_TIMEOUT";
+        case DGT_ERR_UNSUPPORTED: return "DGT_ERR_UNSUPPORTED";
+        default: return "DGT_ERR_UNKNOWN";
+    }
+}
+
+const char* dgt_last_error(void) { return g_last_error.c_str(); }
+
+int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, void* out, int64_t howmany, void* stream) {
+    if (!in || !out || howmany < 0 || (direction != -1 && direction != 1)) return fail(DGT_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == DGT_F32) {
+        TwTable<float> t;
+        if (!radix_plan(n, t.ref.pl) || n + 1 > tile_cap<float>())
+            return fail(DGT_ERR_UNSUPPORTED, "length %lld", (long long)n);
+        std::vector<double> h(2 * n);
+        for (int64_t e = 0; e < n; ++e) cis_host(-e, n, h[2 * e], h[2 * e + 1]);
+        DGT_TRY(upload_cplx<float>(t.buf, h, st));
+        t.ref.tw = t.buf.p;
+        CUDA_TRY(launch_fft_rows_test<float>((const float2*)in, (float2*)out, t.ref, direction, howmany, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        TwTable<double> t;
+        if (!radix_plan(n, t.ref.pl) || n + 1 > tile_cap<double>())
+            return fail(DGT_ERR_UNSUPPORTED, "length %lld", (long long)n);
+        std::vector<double> h(2 * n);
+        for (int64_t e = 0; e < n; ++e) cis_host(-e, n, h[2 * e], h[2 * e + 1]);
+        DGT_TRY(upload_cplx<double>(t.buf, h, st));
+        t.ref.tw = t.buf.p;
+        CUDA_TRY(launch_fft_rows_test<double>((const double2*)in, (double2*)out, t.ref, direction, howmany, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return DGT_OK;
+}
+
+}  // extern "C"
