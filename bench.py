@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""DGT coefficient throughput on one GB300: the audio batch workload.
+
+Workload: 64 real pink-noise signals, L = 2^20, a = 128, M = 1024 (N = 8192, b = 1024),
+quincunx lattice lambda = 1/2; windows: Hann FIR of length 1024 and the full-length
+Gaussian of width sqrt(L).  One step, in float32 on the whole batch:
+
+    Hann (FIR route):          analysis  +  synthesis with the canonical dual
+    Gaussian (shear route):    analysis  +  synthesis with the canonical dual
+    Gaussian (coset route):    analysis  +  synthesis with the canonical dual
+
+value = DGT coefficients produced or consumed per second over the batch
+(6 * 64 * M * N per step), device-timed with CUDA events, inputs resident in HBM.
+The same step in float64 is timed separately ("fp64").  Multi-GPU runs are independent
+replicas (weak scaling), one process per GPU under torchrun.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DGT coeffs/sec FP32 vs FP64 on 1 GB300, % HBM roofline; serve p50/p99 ms"
+UNIT = "coef/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# -------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# -------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append((time.time(), parts))
+
+    def mark(self):
+        return time.time()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [p for (t, p) in self.rows if t0 - 0.15 <= t <= t1 + 0.15] or [p for (_, p) in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(p[1]) for p in rows if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in rows if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in rows for i in range(4) if p[5 + i].lower().startswith("active")})
+        pw = [float(p[3]) for p in rows if p[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# -------------------------------------------------------------------------------------
+# the step
+# -------------------------------------------------------------------------------------
+def make_plans(w, prec, torch):
+    from paper_1307_4569_gb300 import Plan
+    from workloads import gaussian_window, hann_taps
+
+    taps, center = hann_taps(1024)
+    taps = taps / math.sqrt(float((taps ** 2).sum()))
+    g = gaussian_window(w.L)
+    plans = [
+        ("hann-fir", Plan(w.L, w.a, w.M, w.lam1, w.lam2, taps, route="fir", precision=prec, fir_center=center)),
+        ("gauss-shear", Plan(w.L, w.a, w.M, w.lam1, w.lam2, g, route="shear", precision=prec)),
+        ("gauss-coset", Plan(w.L, w.a, w.M, w.lam1, w.lam2, g, route="coset", precision=prec)),
+    ]
+    for _, p in plans:
+        p.dual_window()                      # plan-time set-up, outside every timed region
+    torch.cuda.synchronize()
+    return plans
+
+
+def algorithmic_bytes(name, w, B, csz, rsz, J):
+    """Compulsory bytes of one launch of a hot-path kernel for B signals (inputs + outputs)."""
+    L, MN = w.L, w.M * w.N
+    table = {
+        "fir_analysis": B * (L * rsz + MN * csz),
+        "fir_synthesis": B * (MN * csz + L * rsz),
+        "zak_fwd": B * (L * rsz + L * csz),
+        "prod_ifft": B * (L * csz + MN * csz),
+        "fft_post": B * 2 * MN * csz,
+        "pre_ifft": B * 2 * MN * csz,
+        "fft_prod_adj": B * (MN * csz + L * csz),
+        "zak_inv": B * (L * csz + L * rsz),
+    }
+    return table.get(name)
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1307_4569_gb300 import _capi as K
+    from workloads import AUDIO_BATCH, signal_batch
+
+    w = AUDIO_BATCH
+    B = w.batch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    from paper_1307_4569_gb300 import build as bld
+
+    bld.build()
+
+    f_host = torch.from_numpy(signal_batch(w, cfg_id=1).astype(np.float32)).pin_memory()
+    f = f_host.to(dev)
+    coefs_per_step = 6 * B * w.M * w.N
+
+    def step(plans, fin, cbuf, fr):
+        for _, p in plans:
+            p.dgt(fin, out=cbuf)
+            p.idgt(cbuf, window="dual", real=True, out=fr)
+
+    def timed(plans, fin, cbuf, fr, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step(plans, fin, cbuf, fr)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            K.check(K.lib().dgt_profile_start())
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.time()
+        e0.record()
+        for _ in range(steps):
+            step(plans, fin, cbuf, fr)
+        e1.record()
+        torch.cuda.synchronize()
+        t1 = time.time()
+        prof = None
+        if profile:
+            buf = __import__("ctypes").create_string_buffer(1 << 16)
+            K.check(K.lib().dgt_profile_stop(buf, len(buf)))
+            prof = json.loads(buf.value.decode())
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, t0, t1
+
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    # ---------------- float32 (the headline) ----------------
+    plans = make_plans(w, "f32", torch)
+    cbuf = torch.empty((B, w.N, w.M), dtype=torch.complex64, device=dev)
+    fr = torch.empty((B, w.L), dtype=torch.float32, device=dev)
+    clocks.start()
+    time.sleep(0.3)
+    ms, prof, t0, t1 = timed(plans, f, cbuf, fr, args.steps, args.warmup, profile=True)
+    value = world * coefs_per_step / (ms * 1e-3)
+
+    # reconstruction check of the timed output (last variant)
+    err = float(torch.linalg.vector_norm(fr - f) / torch.linalg.vector_norm(f))
+
+    # ---------------- end to end through the public API, pinned host buffers ----------------
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    c_host = torch.empty((B, w.N, w.M), dtype=torch.complex64).pin_memory()
+    fr_host = torch.empty((B, w.L), dtype=torch.float32).pin_memory()
+    fin = torch.empty_like(f)
+
+    def e2e_step():
+        fin.copy_(f_host, non_blocking=True)
+        for _, p in plans:
+            p.dgt(fin, out=cbuf)
+            c_host.copy_(cbuf, non_blocking=True)
+            p.idgt(cbuf, window="dual", real=True, out=fr)
+            fr_host.copy_(fr, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for _ in range(e2e_steps):
+        e2e_step()
+    a1.record()
+    torch.cuda.synchronize()
+    e2e_ms = a0.elapsed_time(a1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    te = time.time()
+    clocks.stop()
+    clk = clocks.summary(t0, te)
+    h2d = B * w.L * 4
+    d2h = 3 * (B * w.N * w.M * 8 + B * w.L * 4)
+
+    # ---------------- float64 comparison (same step, fewer iterations) ----------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        del plans
+        torch.cuda.empty_cache()
+        plans64 = make_plans(w, "f64", torch)
+        f64 = f.double()
+        c64 = torch.empty((B, w.N, w.M), dtype=torch.complex128, device=dev)
+        fr64 = torch.empty((B, w.L), dtype=torch.float64, device=dev)
+        ms64, _, _, _ = timed(plans64, f64, c64, fr64, args.fp64_steps, 1)
+        fp64 = {"value": world * coefs_per_step / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                "steps": args.fp64_steps, "fp32_speedup": ms64 / ms}
+        del plans64, c64, fr64, f64
+        torch.cuda.empty_cache()
+
+    # ---------------- roofline of the dominant kernel ----------------
+    peak, peak_kind = _peaks()
+    kernels = {}
+    total_prof_ms = sum(v["ms"] for v in prof.values()) if prof else 0.0
+    for name, v in (prof or {}).items():
+        ab = algorithmic_bytes(name, w, B, 8, 4, 2)
+        avg = v["ms"] / v["launches"]
+        kernels[name] = {"launches": v["launches"], "ms_per_launch": avg, "share": v["ms"] / total_prof_ms,
+                         "achieved_gbs": (ab / (avg * 1e-3) / 1e9) if ab else None}
+    dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+    roof = None
+    if dom:
+        ab = algorithmic_bytes(dom, w, B, 8, 4, 2)
+        ach = ab / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e9
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tf):
+            try:
+                traffic = json.load(open(tf)).get(dom)
+            except Exception:
+                traffic = None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_kind": peak_kind, "traffic": traffic,
+                "algorithmic_bytes_per_launch": ab}
+    launches = sum(v["launches"] for v in (prof or {}).values())
+    step_bytes = 3 * 2 * B * (w.L * 4 + w.M * w.N * 8)
+    path = {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+            "frac_of_peak": step_bytes / (ms * 1e-3) / 1e9 / peak, "frac_of_8tbs": step_bytes / (ms * 1e-3) / 8e12}
+
+    # ---------------- CPU baseline (oracle), rank 0 only ----------------
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_procs)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "batch": B, "L": w.L, "a": w.a, "M": w.M, "lambda": "%d/%d" % (w.lam1, w.lam2),
+                   "windows": ["hann1024-fir", "gauss-full"], "routes": [n for n, _ in make_plan_names()],
+                   "step": "analysis + dual synthesis for each of hann-fir, gauss-shear, gauss-coset",
+                   "coefs_per_step": coefs_per_step, "l2": "inputs larger than L2 (4.3 GB coefficient array)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "path_roofline": path,
+        "kernels": kernels,
+        "gpu_launches": launches * 1 if launches else 0,
+        "e2e": {"value": world * coefs_per_step / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "steps": e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "fp64": fp64,
+        "clocks": clk,
+        "reconstruction_rel_err": err,
+        "cpu_baseline": cpu,
+    }
+    return line
+
+
+def make_plan_names():
+    return [("hann-fir", None), ("gauss-shear", None), ("gauss-coset", None)]
+
+
+# -------------------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline leg and the reference arm)
+# -------------------------------------------------------------------------------------
+def _oracle_signal_pass(idx):
+    """One signal of the workload through the oracle: analysis + synthesis with the canonical
+    dual for the Hann window (expanded to full length) and the Gaussian on both routes."""
+    import numpy as np
+
+    from oracle import dgt as OD
+    from oracle import duals as OU
+    from workloads import AUDIO_BATCH, gaussian_window, hann_window, signal_batch
+
+    w = AUDIO_BATCH
+    f = signal_batch(w, count=1, cfg_id=1, start=idx)[0]
+    gh = hann_window(w.L, 1024)
+    gg = gaussian_window(w.L)
+    gdh = OU.fir_dual_diag(gh, w.a, w.M)
+    gdg = OU.zak_gram_dual(gg, w.a, w.M, w.lam1, w.lam2)
+    t0 = time.time()
+    c = OD.dgt_coset(f, gh, w.a, w.M, w.lam1, w.lam2)
+    OD.idgt_coset(c, gdh, w.a, w.M, w.lam1, w.lam2)
+    c = OD.dgt_shear(f, gg, w.a, w.M, w.lam1, w.lam2)
+    OD.idgt_shear(c, gdg, w.a, w.M, w.lam1, w.lam2)
+    c = OD.dgt_coset(f, gg, w.a, w.M, w.lam1, w.lam2)
+    OD.idgt_coset(c, gdg, w.a, w.M, w.lam1, w.lam2)
+    return t0, time.time()
+
+
+def cpu_baseline(max_procs=16):
+    """The oracle as it stands on the host cores: one signal per spawned process (numpy's FFT
+    is single-threaded), all processes at once; throughput = coefficients / (last end - first
+    start) over the timed passes (window set-up excluded)."""
+    import multiprocessing as mp
+
+    from workloads import AUDIO_BATCH
+
+    w = AUDIO_BATCH
+    cores = len(os.sched_getaffinity(0))
+    nproc = max(1, min(cores, max_procs))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(nproc) as pool:
+        spans = pool.map(_oracle_signal_pass, range(nproc))
+    wall = max(e for _, e in spans) - min(s for s, _ in spans)
+    single = statistics.median(e - s for s, e in spans)
+    coefs = nproc * 6 * w.M * w.N
+    return {"value": coefs / wall, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": "%d signals of the 64-signal audio batch, one per process; each: analysis + dual synthesis "
+                      "for hann (full-length, coset), gauss shear, gauss coset (median %.1f s per signal)"
+                      % (nproc, single),
+            "host_cores": cores, "single_signal_s": single}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from workloads import AUDIO_BATCH
+
+    w = AUDIO_BATCH
+    cores = 1
+    times = []
+    for i in range(args.steps):
+        s0, s1 = _oracle_signal_pass(i)
+        times.append(s1 - s0)
+    ms = 1e3 * sum(times) / len(times)
+    coefs = 6 * w.M * w.N
+    v = coefs / (ms * 1e-3)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "batch_sample": 1, "L": w.L, "a": w.a, "M": w.M,
+                       "step": "one signal of the batch through the CPU oracle (analysis + dual synthesis, "
+                               "hann / gauss-shear / gauss-coset)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "1 signal per step of the 64-signal batch"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=16)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if world > 1:
+        import torch
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

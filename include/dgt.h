@@ -161,6 +161,14 @@ void dgt_plan_destroy(dgt_plan_t plan);
 const char* dgt_strerror(int status);
 const char* dgt_last_error(void);
 
+/* Per-kernel timing of the hot path.  dgt_profile_start() makes every later analysis,
+ * synthesis and gradient call record a CUDA event pair on its stream around each kernel
+ * launch; dgt_profile_stop() synchronises the device, writes a JSON object
+ * {"kernel": {"launches": n, "ms": total}, ...} into json (cap bytes, NUL-terminated)
+ * and turns recording off.  Not thread-safe; for measurement only. */
+int dgt_profile_start(void);
+int dgt_profile_stop(char* json, size_t cap);
+
 /* Building block check: `howmany` contiguous complex transforms of length n (device buffers),
  * direction -1 (forward) or +1 (unnormalised inverse), precision DGT_F32 / DGT_F64. */
 int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, void* out, int64_t howmany,

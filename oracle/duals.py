@@ -174,7 +174,7 @@ def fir_dual_diag(g, a, M) -> np.ndarray:
     g = np.asarray(g, dtype=np.complex128)
     L = g.shape[0]
     N = L // a
-    den = np.zeros(L)
-    for n in range(N):
-        den += np.abs(np.roll(g, a * n)) ** 2
+    # sum_n |g(l - a n)|^2 depends on l mod a only: the rows of |g|^2 viewed as [N][a], summed
+    per = (np.abs(g) ** 2).reshape(N, a).sum(axis=0)
+    den = np.tile(per, N)
     return g / (M * den)

@@ -110,6 +110,7 @@ template <typename C> struct FirParams {
     const C* taps;                    // Lg taps of the analysis / synthesis window
     CisTable<C> cisLM;                // exp(2 pi i e / (lam2 M))
     int64_t cols;                     // time positions per CTA
+    int64_t group;                    // rows transformed at once (spare buffer rows)
 };
 template <typename T>
 cudaError_t launch_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp,

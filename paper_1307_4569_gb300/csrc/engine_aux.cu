@@ -12,6 +12,22 @@ template <typename C> __device__ __forceinline__ C load_any2(const void* p, int 
     return reinterpret_cast<const C*>(p)[i];
 }
 
+// Transform nr rows (pitch elements apart) in groups of `group` rows, each group ping-ponged
+// with the spare buffer of `group` rows; results end in place.  Ends synchronised.
+template <int DIR, typename C>
+__device__ void fft_rows_grouped(C* rows, C* spare, int nr, int group, int pitch, const FftPlanDev& pl,
+                                 const C* __restrict__ tw) {
+    for (int g0 = 0; g0 < nr; g0 += group) {
+        const int ng = min(group, nr - g0);
+        C* a = rows + (size_t)g0 * pitch;
+        const C* res = fft_tile<DIR, false>(a, spare, pl, ng, 1, pitch, tw);
+        if (res != a) {
+            for (int e = threadIdx.x; e < ng * pitch; e += blockDim.x) a[e] = res[e];
+            __syncthreads();
+        }
+    }
+}
+
 static size_t g_smem_optin2 = 0;
 template <typename K> static cudaError_t prep_smem2(K kernel, size_t bytes) {
     if (g_smem_optin2 == 0) {
@@ -43,7 +59,8 @@ __global__ void __launch_bounds__(kThreadsBig) fir_analysis_kernel(const void* _
     const int nc = (int)min(fp.cols, fp.N - n0);
     const int64_t S = fp.a * (nc - 1) + fp.Lg;                // segment length
     C* rows = reinterpret_cast<C*>(smem_raw);
-    C* seg = rows + 2 * (size_t)fp.cols * pitch;
+    C* spare = rows + (size_t)fp.cols * pitch;
+    C* seg = spare + (size_t)fp.group * pitch;
     const int64_t lstart = fp.a * n0 - fp.center;
     for (int64_t t = threadIdx.x; t < S; t += blockDim.x) {
         const int64_t l = posmod(lstart + t, fp.L);
@@ -67,10 +84,10 @@ __global__ void __launch_bounds__(kThreadsBig) fir_analysis_kernel(const void* _
         rows[r * pitch + k] = h;
     }
     __syncthreads();
-    const C* res = fft_tile<-1, false>(rows, rows + fp.cols * pitch, pl, nc, 1, pitch, tw);
+    fft_rows_grouped<-1>(rows, spare, nc, (int)fp.group, pitch, pl, tw);
     for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
         const int r = e / M, m = e % M;
-        c[(b * fp.N + n0 + r) * fp.M + m] = res[r * pitch + m];
+        c[(b * fp.N + n0 + r) * fp.M + m] = rows[r * pitch + m];
     }
 }
 
@@ -86,7 +103,7 @@ cudaError_t launch_fir_analysis(const void* f, int f_real, cplx<T>* c, const Fir
                                 const FftRef& fm, int64_t B, cudaStream_t st) {
     using C = cplx<T>;
     const int64_t S = fp.a * (fp.cols - 1) + fp.Lg;
-    const size_t smem = sizeof(C) * (2 * (size_t)fp.cols * (fp.M + 1) + S);
+    const size_t smem = sizeof(C) * ((size_t)(fp.cols + fp.group) * (fp.M + 1) + S);
     if (smem > kSmemBudget) return cudaErrorInvalidValue;
     auto k = fir_analysis_kernel<T>;
     cudaError_t e = prep_smem2(k, smem);
@@ -120,12 +137,13 @@ __global__ void __launch_bounds__(kThreadsBig) fir_synthesis_kernel(const cplx<T
     const int64_t n0 = chunk * fp.cols;
     const int nc = (int)fp.cols;
     C* rows = reinterpret_cast<C*>(smem_raw);
+    C* spare = rows + (size_t)fp.cols * pitch;
     for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
         const int r = e / M, m = e % M;
         rows[r * pitch + m] = c[(b * fp.N + n0 + r) * fp.M + m];
     }
     __syncthreads();
-    rows = fft_tile<+1, false>(rows, rows + nc * pitch, pl, nc, 1, pitch, tw);
+    fft_rows_grouped<+1>(rows, spare, nc, (int)fp.group, pitch, pl, tw);
     const int64_t S = fp.a * (nc - 1) + fp.Lg;
     const int64_t ov = fp.Lg > fp.a ? fp.Lg - fp.a : 0;
     const int64_t lstart = fp.a * n0 - fp.center;
@@ -182,7 +200,7 @@ cudaError_t launch_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>*
     using C = cplx<T>;
     if (fp.N % fp.cols) return cudaErrorInvalidValue;
     if (fp.a * fp.cols < fp.Lg - fp.a) return cudaErrorInvalidValue;
-    const size_t smem = 2 * sizeof(C) * ((size_t)fp.cols * (fp.M + 1));
+    const size_t smem = sizeof(C) * ((size_t)(fp.cols + fp.group) * (fp.M + 1));
     if (smem > kSmemBudget) return cudaErrorInvalidValue;
     auto k = fir_synthesis_kernel<T>;
     cudaError_t e = prep_smem2(k, smem);

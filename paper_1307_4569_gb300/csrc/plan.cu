@@ -46,6 +46,43 @@ static int fail(int status, const char* fmt, ...) {
     } while (0)
 
 // ---------------------------------------------------------------------------------------
+// optional per-kernel timing: CUDA events recorded on the launching stream around every
+// hot-path launch while profiling is on (dgt_profile_start / dgt_profile_stop)
+// ---------------------------------------------------------------------------------------
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_prof_pool;
+static size_t g_prof_used = 0;
+
+static cudaEvent_t prof_event() {
+    if (g_prof_used == g_prof_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        g_prof_pool.push_back(e);
+    }
+    return g_prof_pool[g_prof_used++];
+}
+
+#define KTRY(NAME, ST, ...)                                           \
+    do {                                                              \
+        cudaEvent_t _ka = nullptr, _kb = nullptr;                     \
+        if (g_prof_on) {                                              \
+            _ka = prof_event();                                       \
+            _kb = prof_event();                                       \
+            cudaEventRecord(_ka, ST);                                 \
+        }                                                             \
+        CUDA_TRY(__VA_ARGS__);                                        \
+        if (g_prof_on) {                                              \
+            cudaEventRecord(_kb, ST);                                 \
+            g_prof.push_back({NAME, _ka, _kb});                       \
+        }                                                             \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------
 // integer lattice algebra (exact, int64)
 // ---------------------------------------------------------------------------------------
 static int64_t igcd(int64_t x, int64_t y) {
@@ -229,7 +266,8 @@ struct PlanCore {
     // Algorithm 1 constants (frequency-shear branch)
     int64_t ar = 0, Mr = 0, Nr = 0, C1 = 0, C2 = 0, C3m = 0, C4m = 0, C5m = 0, C6 = 0;
     int64_t L1 = 0, L2 = 0;            // FFT_L split
-    int64_t fir_cols = 0;
+    int64_t fir_cols = 0, fir_group = 1;
+    bool fir_synth_ok = true;
     std::vector<double> g_host;        // window as given (complex interleaved, float64)
     SepGeom coset_sep{};               // (lam2 a, M): used by the dual / tight Gram blocks
 };
@@ -465,25 +503,25 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         }
         if (k.route == DGT_ROUTE_FIR) {
             FirParams<C> fp = fir_params((const C*)gT.p);
-            CUDA_TRY(launch_fir_analysis<T>(f, f_real, (C*)c, fp, *fft(k.M), B, st));
+            KTRY("fir_analysis", st, launch_fir_analysis<T>(f, f_real, (C*)c, fp, *fft(k.M), B, st));
             return DGT_OK;
         }
         C* zf = (C*)(ws + ly.zf);
         C* y = (C*)(ws + ly.y);
         const FftRef* fd = fft(k.sep.d);
         if (k.route == DGT_ROUTE_COSET) {
-            CUDA_TRY(launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, k.sep.d, *fd, nochirp(), B, st));
+            KTRY("zak_fwd", st, launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, k.sep.d, *fd, nochirp(), B, st));
         } else if (!k.freq_shear) {
-            CUDA_TRY(launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 0), B, st));
+            KTRY("zak_fwd", st, launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 0), B, st));
         } else {
             C* tmp = (C*)(ws + ly.tmp);
             C* fh = (C*)(ws + ly.fh);
-            CUDA_TRY(launch_fftL_cols<T>(f, f_real, tmp, k.L1, k.L2, -1, *fft(k.L1), chirp(k.sh.s1, 0), cisL.tab, B, st));
-            CUDA_TRY(launch_fftL_rows<T>(tmp, fh, 0, k.L1, k.L2, -1, *fft(k.L2), chirp(-k.sh.s0, 0), (T)1, B, st));
-            CUDA_TRY(launch_zak_fwd<T>(fh, 0, k.L, zf, k.L, k.L, k.sep.d, *fd, nochirp(), B, st));
+            KTRY("fftL_cols", st, launch_fftL_cols<T>(f, f_real, tmp, k.L1, k.L2, -1, *fft(k.L1), chirp(k.sh.s1, 0), cisL.tab, B, st));
+            KTRY("fftL_rows", st, launch_fftL_rows<T>(tmp, fh, 0, k.L1, k.L2, -1, *fft(k.L2), chirp(-k.sh.s0, 0), (T)1, B, st));
+            KTRY("zak_fwd", st, launch_zak_fwd<T>(fh, 0, k.L, zf, k.L, k.L, k.sep.d, *fd, nochirp(), B, st));
         }
-        CUDA_TRY(launch_prod_ifft<T>(zf, (const C*)zg[0].p, k.J, y, k.sep, *fd, B, st));
-        CUDA_TRY(launch_fft_post<T>(y, (C*)c, k.sep, k.J, *fft(k.sep.M), post(), B, st));
+        KTRY("prod_ifft", st, launch_prod_ifft<T>(zf, (const C*)zg[0].p, k.J, y, k.sep, *fd, B, st));
+        KTRY("fft_post", st, launch_fft_post<T>(y, (C*)c, k.sep, k.J, *fft(k.sep.M), post(), B, st));
         return DGT_OK;
     }
 
@@ -492,6 +530,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         FirParams<C> fp{};
         fp.L = k.L; fp.a = k.a; fp.M = k.M; fp.N = k.N; fp.lam1 = k.lam1; fp.lam2 = k.lam2;
         fp.Lg = k.Lg; fp.center = k.center; fp.taps = taps; fp.cisLM = cisLM.tab; fp.cols = k.fir_cols;
+        fp.group = k.fir_group;
         return fp;
     }
 
@@ -593,27 +632,30 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             ws = (char*)work.p;
         }
         if (k.route == DGT_ROUTE_FIR) {
+            if (!k.fir_synth_ok)
+                return fail(DGT_ERR_UNSUPPORTED, "FIR synthesis: %lld columns per tile cannot cover a window of %lld",
+                            (long long)k.fir_cols, (long long)k.Lg);
             const C* taps = which == 0 ? (const C*)gT.p : (const C*)gam[which].p;
             FirParams<C> fp = fir_params(taps);
-            CUDA_TRY(launch_fir_synthesis<T>((const C*)c, f, f_real, (C*)(ws + ly.seams), fp, *fft(k.M), B, st));
+            KTRY("fir_synthesis", st, launch_fir_synthesis<T>((const C*)c, f, f_real, (C*)(ws + ly.seams), fp, *fft(k.M), B, st));
             return DGT_OK;
         }
         C* zf = (C*)(ws + ly.zf);
         C* y = (C*)(ws + ly.y);
         const FftRef* fd = fft(k.sep.d);
-        CUDA_TRY(launch_pre_ifft<T>((const C*)c, y, k.sep, k.J, *fft(k.sep.M), post(), B, st));
-        CUDA_TRY(launch_fft_prod_adj<T>(y, (const C*)zg[which].p, k.J, zf, k.sep, *fd, B, st));
+        KTRY("pre_ifft", st, launch_pre_ifft<T>((const C*)c, y, k.sep, k.J, *fft(k.sep.M), post(), B, st));
+        KTRY("fft_prod_adj", st, launch_fft_prod_adj<T>(y, (const C*)zg[which].p, k.J, zf, k.sep, *fd, B, st));
         if (k.route == DGT_ROUTE_COSET) {
-            CUDA_TRY(launch_zak_inv<T>(zf, k.L, f, f_real, k.L, k.L, k.sep.d, *fd, nochirp(), (T)1, B, st));
+            KTRY("zak_inv", st, launch_zak_inv<T>(zf, k.L, f, f_real, k.L, k.L, k.sep.d, *fd, nochirp(), (T)1, B, st));
         } else if (!k.freq_shear) {
-            CUDA_TRY(launch_zak_inv<T>(zf, k.L, f, f_real, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 1), (T)1, B, st));
+            KTRY("zak_inv", st, launch_zak_inv<T>(zf, k.L, f, f_real, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 1), (T)1, B, st));
         } else {
             C* tmp = (C*)(ws + ly.tmp);
             C* fh = (C*)(ws + ly.fh);
-            CUDA_TRY(launch_zak_inv<T>(zf, k.L, fh, 0, k.L, k.L, k.sep.d, *fd, nochirp(), (T)1, B, st));
+            KTRY("zak_inv", st, launch_zak_inv<T>(zf, k.L, fh, 0, k.L, k.L, k.sep.d, *fd, nochirp(), (T)1, B, st));
             // adjoint of f -> pchirp(-s0) FFT(pchirp(s1) f): conj chirps, unnormalised inverse DFT
-            CUDA_TRY(launch_fftL_cols<T>(fh, 0, tmp, k.L1, k.L2, +1, *fft(k.L1), chirp(-k.sh.s0, 1), cisL.tab, B, st));
-            CUDA_TRY(launch_fftL_rows<T>(tmp, f, f_real, k.L1, k.L2, +1, *fft(k.L2), chirp(k.sh.s1, 1), (T)1, B, st));
+            KTRY("fftL_cols", st, launch_fftL_cols<T>(fh, 0, tmp, k.L1, k.L2, +1, *fft(k.L1), chirp(-k.sh.s0, 1), cisL.tab, B, st));
+            KTRY("fftL_rows", st, launch_fftL_rows<T>(tmp, f, f_real, k.L1, k.L2, +1, *fft(k.L2), chirp(k.sh.s1, 1), (T)1, B, st));
         }
         return DGT_OK;
     }
@@ -665,11 +707,11 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         C* y = (C*)p; p += al(sizeof(C) * (size_t)B * k.M * k.N);
         C* v = (C*)p; p += al(sizeof(C) * (size_t)k.lam2 * k.L);
         C* wj = (C*)p;
-        CUDA_TRY(launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, cg.d, *fd, nochirp(), B, st));
-        CUDA_TRY(launch_pre_ifft<T>((const C*)G, y, cg, k.lam2, *fft(cg.M), pp, B, st));
-        CUDA_TRY(launch_fft_grad_window<T>(y, zf, k.lam2, v, cg, *fd, B, st));
-        CUDA_TRY(launch_zak_inv<T>(v, k.L, wj, 0, k.L, k.L, cg.d, *fd, nochirp(), (T)1, k.lam2, st));
-        CUDA_TRY(launch_grad_window_combine<T>(wj, grad, grad_real, k.L, k.a, k.lam2, (const int64_t*)sigma.p,
+        KTRY("zak_fwd", st, launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, cg.d, *fd, nochirp(), B, st));
+        KTRY("pre_ifft", st, launch_pre_ifft<T>((const C*)G, y, cg, k.lam2, *fft(cg.M), pp, B, st));
+        KTRY("fft_grad_window", st, launch_fft_grad_window<T>(y, zf, k.lam2, v, cg, *fd, B, st));
+        KTRY("zak_inv", st, launch_zak_inv<T>(v, k.L, wj, 0, k.L, k.L, cg.d, *fd, nochirp(), (T)1, k.lam2, st));
+        KTRY("grad_window_combine", st, launch_grad_window_combine<T>(wj, grad, grad_real, k.L, k.a, k.lam2, (const int64_t*)sigma.p,
                                                cisL.tab, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         return DGT_OK;
@@ -678,7 +720,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) override {
         const PlanCore& k = core;
         DGT_TRY(lossparts.alloc(sizeof(double) * 64 * B));
-        CUDA_TRY(launch_logmag<T>((const C*)c, (C*)G, (double*)lossparts.p, k.M * k.N, (T)eps, B, st));
+        KTRY("logmag", st, launch_logmag<T>((const C*)c, (C*)G, (double*)lossparts.p, k.M * k.N, (T)eps, B, st));
         std::vector<double> h(64 * B);
         CUDA_TRY(cudaMemcpyAsync(h.data(), lossparts.p, sizeof(double) * 64 * B, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -747,8 +789,26 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
     if (!shear_select(L, a, k.b, k.s, k.sh)) return fail(DGT_ERR_ARG, "no shear found");
     k.freq_shear = k.sh.s0 != 0;
 
+    // FIR chunking: columns per CTA, a divisor of N, fitting the shared-memory tile;
+    // synthesis also needs a * cols >= Lg - a so that only neighbouring chunks overlap
+    int64_t fir_cols = 0;
+    bool fir_synth_ok = false;
+    if (g->kind == DGT_WINDOW_FIR && fft_ok(M, precision)) {
+        const size_t csz = precision == DGT_F64 ? 16 : 8;
+        const int64_t need = std::max<int64_t>(1, (g->len + a - 1) / a);
+        auto fits = [&](int64_t cc) {
+            const int64_t grp = std::min<int64_t>(cc, 4);
+            return csz * ((size_t)(cc + grp) * (M + 1) + (size_t)(a * (cc - 1) + g->len)) <= kSmemBudget;
+        };
+        for (int64_t cc = 64; cc >= 1 && !fir_cols; --cc)
+            if (k.N % cc == 0 && cc >= need && fits(cc)) fir_cols = cc;
+        fir_synth_ok = fir_cols > 0;
+        for (int64_t cc = 64; cc >= 1 && !fir_cols; --cc)
+            if (k.N % cc == 0 && fits(cc)) fir_cols = cc;
+        if (fir_cols && !fir_synth_ok) fir_synth_ok = a * fir_cols >= g->len - a;
+    }
     if (route == DGT_ROUTE_AUTO) {
-        if (g->kind == DGT_WINDOW_FIR) route = DGT_ROUTE_FIR;
+        if (g->kind == DGT_WINDOW_FIR && fir_cols && fir_synth_ok) route = DGT_ROUTE_FIR;
         else route = k.freq_shear ? DGT_ROUTE_COSET : DGT_ROUTE_SHEAR;
     }
     if (route == DGT_ROUTE_FIR && g->kind != DGT_WINDOW_FIR)
@@ -771,22 +831,10 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
 
     if (route == DGT_ROUTE_FIR) {
         if (!fft_ok(M, precision)) return fail(DGT_ERR_UNSUPPORTED, "FFT length M=%lld unsupported", (long long)M);
-        // columns per CTA: a divisor of N, at least ceil(Lg/a), fitting the shared-memory tile
-        const size_t csz = precision == DGT_F64 ? 16 : 8;
-        const int64_t need = std::max<int64_t>(1, (k.Lg + a - 1) / a);
-        auto fits = [&](int64_t cc) {
-            return csz * (2 * (size_t)cc * (M + 1) + (size_t)(a * (cc - 1) + k.Lg)) <= kSmemBudget;
-        };
-        int64_t best = 0;
-        for (int64_t cc = 64; cc >= 1; --cc)
-            if (k.N % cc == 0 && cc >= need && fits(cc)) { best = cc; break; }
-        if (best == 0) {
-            // analysis works with any chunking; synthesis needs the seam condition
-            for (int64_t cc = 64; cc >= 1; --cc)
-                if (k.N % cc == 0 && fits(cc)) { best = cc; break; }
-        }
-        if (best == 0) return fail(DGT_ERR_UNSUPPORTED, "FIR route: M=%lld too long for one tile", (long long)M);
-        k.fir_cols = best;
+        if (!fir_cols) return fail(DGT_ERR_UNSUPPORTED, "FIR route: M=%lld too long for one tile", (long long)M);
+        k.fir_cols = fir_cols;
+        k.fir_group = std::min<int64_t>(fir_cols, 4);
+        k.fir_synth_ok = fir_synth_ok;
     } else if (route == DGT_ROUTE_COSET) {
         k.sep = make_sep(L, lam2 * a, M);
         k.J = lam2;
@@ -963,6 +1011,44 @@ const char* dgt_strerror(int status) {
 }
 
 const char* dgt_last_error(void) { return g_last_error.c_str(); }
+
+int dgt_profile_start(void) {
+    g_prof.clear();
+    g_prof_used = 0;
+    g_prof_on = true;
+    return DGT_OK;
+}
+
+int dgt_profile_stop(char* json, size_t cap) {
+    g_prof_on = false;
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::map<std::string, std::pair<int64_t, double>> acc;
+    for (const ProfRec& r : g_prof) {
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+        auto& v = acc[r.name];
+        v.first += 1;
+        v.second += ms;
+    }
+    std::string out = "{";
+    bool first = true;
+    for (auto& kv : acc) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f}", first ? "" : ", ",
+                 kv.first.c_str(), (long long)kv.second.first, kv.second.second);
+        out += buf;
+        first = false;
+    }
+    out += "}";
+    g_prof.clear();
+    g_prof_used = 0;
+    if (json && cap) {
+        strncpy(json, out.c_str(), cap - 1);
+        json[cap - 1] = 0;
+        if (out.size() >= cap) return fail(DGT_ERR_ARG, "profile buffer too small (%zu bytes needed)", out.size() + 1);
+    }
+    return DGT_OK;
+}
 
 int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, void* out, int64_t howmany, void* stream) {
     if (!in || !out || howmany < 0 || (direction != -1 && direction != 1)) return fail(DGT_ERR_ARG, "bad argument");
