@@ -791,21 +791,27 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
 
     // FIR chunking: columns per CTA, a divisor of N, fitting the shared-memory tile;
     // synthesis also needs a * cols >= Lg - a so that only neighbouring chunks overlap
-    int64_t fir_cols = 0;
+    int64_t fir_cols = 0, fir_group = 1;
     bool fir_synth_ok = false;
     if (g->kind == DGT_WINDOW_FIR && fft_ok(M, precision)) {
         const size_t csz = precision == DGT_F64 ? 16 : 8;
         const int64_t need = std::max<int64_t>(1, (g->len + a - 1) / a);
-        auto fits = [&](int64_t cc) {
-            const int64_t grp = std::min<int64_t>(cc, 4);
-            return csz * ((size_t)(cc + grp) * (M + 1) + (size_t)(a * (cc - 1) + g->len)) <= kSmemBudget;
+        // spare rows for the grouped FFT: the largest of 4, 2, 1 with which both the analysis
+        // tile (rows + spare + input segment) and the synthesis tile (rows + spare) fit
+        auto group_for = [&](int64_t cc) -> int64_t {
+            for (int64_t grp : {4, 2, 1}) {
+                if (grp > cc) continue;
+                if (csz * ((size_t)(cc + grp) * (M + 1) + (size_t)(a * (cc - 1) + g->len)) <= kSmemBudget) return grp;
+            }
+            return 0;
         };
         for (int64_t cc = 64; cc >= 1 && !fir_cols; --cc)
-            if (k.N % cc == 0 && cc >= need && fits(cc)) fir_cols = cc;
+            if (k.N % cc == 0 && cc >= need && group_for(cc)) fir_cols = cc;
         fir_synth_ok = fir_cols > 0;
         for (int64_t cc = 64; cc >= 1 && !fir_cols; --cc)
-            if (k.N % cc == 0 && fits(cc)) fir_cols = cc;
+            if (k.N % cc == 0 && group_for(cc)) fir_cols = cc;
         if (fir_cols && !fir_synth_ok) fir_synth_ok = a * fir_cols >= g->len - a;
+        fir_group = fir_cols ? group_for(fir_cols) : 1;
     }
     if (route == DGT_ROUTE_AUTO) {
         if (g->kind == DGT_WINDOW_FIR && fir_cols && fir_synth_ok) route = DGT_ROUTE_FIR;
@@ -833,7 +839,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
         if (!fft_ok(M, precision)) return fail(DGT_ERR_UNSUPPORTED, "FFT length M=%lld unsupported", (long long)M);
         if (!fir_cols) return fail(DGT_ERR_UNSUPPORTED, "FIR route: M=%lld too long for one tile", (long long)M);
         k.fir_cols = fir_cols;
-        k.fir_group = std::min<int64_t>(fir_cols, 4);
+        k.fir_group = fir_group;
         k.fir_synth_ok = fir_synth_ok;
     } else if (route == DGT_ROUTE_COSET) {
         k.sep = make_sep(L, lam2 * a, M);
