@@ -143,6 +143,23 @@ int dgt_window_tight(dgt_plan_t plan, void* gt_out, void* stream);
 int dgt_grad_window(dgt_plan_t plan, const void* f, int f_is_real, const void* G, void* grad_g, int grad_real,
                     int64_t batch, void* stream);
 
+/* Allocation-free FIR synthesis.  For callers that must not allocate device memory while
+ * they run -- a real-time audio callback cannot wait on cudaMalloc, which may synchronise the
+ * device and take driver locks; a plug-in host may own all device memory; a process may have
+ * fenced off its allocation budget.  Same result as idgt_exec on an FIR-route plan, but the
+ * scratch that holds the overlap seams between neighbouring column chunks lives in one fixed
+ * 4 MiB array that the library keeps on every GPU that loads it, until the process exits; the
+ * seams need batch * (N / chunk columns) * 2 * (Lg - a) complex values, and a call needing
+ * more than 4 MiB returns DGT_ERR_UNSUPPORTED.  Nothing in the array has to start at zero:
+ * each call writes every scratch element it later reads.  All calls share the array, so calls
+ * that overlap on the GPU (other streams, other threads) race; serialise them.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress): make that first
+ * call before any stream capture.  The dual / tight window must already be cached
+ * (dgt_window_dual / dgt_window_tight), else DGT_ERR_ARG.  The paper has no counterpart:
+ * this is a deployment variant of the weighted overlap-add synthesis. */
+int dgt_fir_synthesis_noalloc(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch,
+                              int which_window, void* stream);
+
 /* Log-magnitude loss helper: loss_b = sum log(|c|^2 + eps) per signal (float64, device array of
  * `batch`), and G = 2 c / (|c|^2 + eps) (device, may be NULL). */
 int dgt_logmag_loss(dgt_plan_t plan, const void* c, void* G, double* loss_dev, double eps, int64_t batch,

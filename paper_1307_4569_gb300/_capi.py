@@ -58,6 +58,7 @@ SIGNATURES = {
     "dgt_window_tight": (i32, [vp, vp, vp]),
     "dgt_grad_window": (i32, [vp, vp, i32, vp, vp, i32, i64, vp]),
     "dgt_logmag_loss": (i32, [vp, vp, vp, vp, C.c_double, i64, vp]),
+    "dgt_fir_synthesis_noalloc": (i32, [vp, vp, vp, i32, i64, i32, vp]),
     "dgt_plan_bytes": (i32, [vp, C.POINTER(C.c_size_t)]),
     "dgt_sync": (i32, [vp]),
     "dgt_plan_destroy": (None, [vp]),

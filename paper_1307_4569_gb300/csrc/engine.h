@@ -140,6 +140,11 @@ cudaError_t launch_gram_solve(const double2* zg, int64_t J, double2* zout, const
 cudaError_t launch_fir_dual(const double2* taps, double2* out, int64_t Lg, int64_t a, int64_t M, int tight,
                             int* status, cudaStream_t st);
 
+// Fixed scratch for the allocation-free FIR synthesis entry point (bytes per GPU), and its
+// device address on the current device (looked up on the first call per device).
+constexpr size_t kNoAllocScratchBytes = (size_t)4 << 20;
+cudaError_t noalloc_scratch(void** out);
+
 // FFT self-test (batched transforms along contiguous rows)
 template <typename T>
 cudaError_t launch_fft_rows_test(const cplx<T>* in, cplx<T>* out, const FftRef& f, int dir, int64_t rows,

@@ -3,6 +3,8 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 namespace dgt {
 
@@ -502,6 +504,32 @@ cudaError_t launch_fir_dual(const double2* taps, double2* out, int64_t Lg, int64
     fir_dual_kernel<<<(unsigned)std::min<int64_t>((Lg + 255) / 256, 1024), 256, 0, st>>>(taps, out, Lg, a, M, tight,
                                                                                          status);
     return cudaGetLastError();
+}
+
+// =====================================================================================
+// Scratch of the allocation-free FIR synthesis entry point: one fixed array per GPU that
+// loads the library, held until the process exits.  Host code must not use the symbol as
+// a pointer: its device address comes from cudaGetSymbolAddress, looked up once per device.
+// =====================================================================================
+static __device__ __align__(256) unsigned char g_fir_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static std::map<int, void*> g_noalloc_addr;
+
+cudaError_t noalloc_scratch(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it == g_noalloc_addr.end()) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_fir_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        it = g_noalloc_addr.emplace(dev, p).first;
+    }
+    *out = it->second;
+    return cudaSuccess;
 }
 
 #define DGT_INST_AUX(T)                                                                                               \

@@ -282,6 +282,7 @@ struct dgt_plan_s {
     virtual int grad_window(const void* f, int f_real, const void* G, void* grad, int grad_real, int64_t B,
                             cudaStream_t st) = 0;
     virtual int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) = 0;
+    virtual int fir_synthesis_noalloc(const void* c, void* f, int f_real, int64_t B, int which, cudaStream_t st) = 0;
     virtual size_t ws_bytes(int64_t B) const = 0;
     virtual size_t owned_bytes() const = 0;
 };
@@ -717,6 +718,29 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         return DGT_OK;
     }
 
+    // FIR synthesis whose seam scratch is the library's fixed per-GPU array: no allocation.
+    int fir_synthesis_noalloc(const void* c, void* f, int f_real, int64_t B, int which, cudaStream_t st) override {
+        const PlanCore& k = core;
+        if (which < 0 || which > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which);
+        if (k.route != DGT_ROUTE_FIR) return fail(DGT_ERR_ARG, "allocation-free synthesis needs an FIR-route plan");
+        if (!k.fir_synth_ok)
+            return fail(DGT_ERR_UNSUPPORTED, "FIR synthesis: %lld columns per tile cannot cover a window of %lld",
+                        (long long)k.fir_cols, (long long)k.Lg);
+        if (!zg_ok[which])
+            return fail(DGT_ERR_ARG, "the dual / tight window is not cached yet (call dgt_window_dual/_tight first)");
+        if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+        const C* taps = which == 0 ? (const C*)gT.p : (const C*)gam[which].p;
+        FirParams<C> fp = fir_params(taps);
+        const size_t need = sizeof(C) * (size_t)B * fir_seam_elems(fp);
+        if (need > kNoAllocScratchBytes)
+            return fail(DGT_ERR_UNSUPPORTED, "allocation-free synthesis needs %zu bytes of scratch; the fixed array holds %zu",
+                        need, kNoAllocScratchBytes);
+        void* scratch = nullptr;
+        CUDA_TRY(noalloc_scratch(&scratch));
+        CUDA_TRY(launch_fir_synthesis<T>((const C*)c, f, f_real, (C*)scratch, fp, *fft(k.M), B, st));
+        return DGT_OK;
+    }
+
     int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) override {
         const PlanCore& k = core;
         DGT_TRY(lossparts.alloc(sizeof(double) * 64 * B));
@@ -977,6 +1001,12 @@ int dgt_grad_window(dgt_plan_t plan, const void* f, int f_is_real, const void* G
                     int64_t batch, void* stream) {
     if (!plan || !f || !G || !grad_g || batch <= 0) return fail(DGT_ERR_ARG, "bad argument");
     return plan->grad_window(f, f_is_real, G, grad_g, grad_real, batch, (cudaStream_t)stream);
+}
+
+int dgt_fir_synthesis_noalloc(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
+                              void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    return plan->fir_synthesis_noalloc(c, f, f_real_out, batch, which_window, (cudaStream_t)stream);
 }
 
 int dgt_logmag_loss(dgt_plan_t plan, const void* c, void* G, double* loss_dev, double eps, int64_t batch, void* stream) {
