@@ -144,14 +144,14 @@ def run_ours(args, rank, world):
     from workloads import AUDIO_BATCH, signal_batch
 
     w = AUDIO_BATCH
-    B = w.batch
+    B = args.batch or w.batch
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     from paper_1307_4569_gb300 import build as bld
 
     bld.build()
 
-    f_host = torch.from_numpy(signal_batch(w, cfg_id=1).astype(np.float32)).pin_memory()
+    f_host = torch.from_numpy(signal_batch(w, count=B, cfg_id=1).astype(np.float32)).pin_memory()
     f = f_host.to(dev)
     coefs_per_step = 6 * B * w.M * w.N
 
@@ -402,6 +402,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-procs", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=0, help="signals per step (default: the workload's 64)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
