@@ -150,6 +150,33 @@ template <typename T>
 cudaError_t launch_fft_rows_test(const cplx<T>* in, cplx<T>* out, const FftRef& f, int dir, int64_t rows,
                                  cudaStream_t st);
 
+// Power-of-two fast path (kernels_p2.cuh); each returns cudaErrorNotSupported when the length
+// or geometry is outside it, and the caller then uses the generic kernel.
+template <typename T>
+cudaError_t p2_zak_fwd(const void* src, int src_real, int64_t sbs, cplx<T>* zf, int64_t zbs, int64_t d, int64_t K0,
+                       const void* tw, const ChirpParams<cplx<T>>& pre, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t p2_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T>* y, const SepGeom& g, const void* tw,
+                         int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t p2_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
+                            const void* tw, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
+                       const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t p2_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const void* tw,
+                        const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t p2_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const void* tw,
+                        const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t p2_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp, const void* tw,
+                            int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t p2_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
+                             const void* tw, int64_t B, cudaStream_t st);
+
 // CTA sizing: largest FFT tile (elements, two ping-pong buffers) that fits the budget
 template <typename T> constexpr int64_t tile_cap() { return (int64_t)(kSmemBudget / (2 * sizeof(cplx<T>))); }
 

@@ -104,6 +104,10 @@ template <typename T>
 cudaError_t launch_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp,
                                 const FftRef& fm, int64_t B, cudaStream_t st) {
     using C = cplx<T>;
+    {
+        const cudaError_t e = p2_fir_analysis<T>(f, f_real, c, fp, fm.tw, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     const int64_t S = fp.a * (fp.cols - 1) + fp.Lg;
     const size_t smem = sizeof(C) * ((size_t)(fp.cols + fp.group) * (fp.M + 1) + S);
     if (smem > kSmemBudget) return cudaErrorInvalidValue;
@@ -204,14 +208,17 @@ cudaError_t launch_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>*
     if (fp.a * fp.cols < fp.Lg - fp.a) return cudaErrorInvalidValue;
     const size_t smem = sizeof(C) * ((size_t)(fp.cols + fp.group) * (fp.M + 1));
     if (smem > kSmemBudget) return cudaErrorInvalidValue;
-    auto k = fir_synthesis_kernel<T>;
-    cudaError_t e = prep_smem2(k, smem);
-    if (e != cudaSuccess) return e;
-    const int thr = threads_for(fp.cols * fp.M);
     const int64_t nchunks = fp.N / fp.cols;
-    dim3 grid((unsigned)nchunks, (unsigned)B);
-    k<<<grid, thr, smem, st>>>(c, f, f_real, seams, fp, fm.pl, (const C*)fm.tw);
-    e = cudaGetLastError();
+    cudaError_t e = p2_fir_synthesis<T>(c, f, f_real, seams, fp, fm.tw, B, st);
+    if (e == cudaErrorNotSupported) {
+        auto k = fir_synthesis_kernel<T>;
+        e = prep_smem2(k, smem);
+        if (e != cudaSuccess) return e;
+        const int thr = threads_for(fp.cols * fp.M);
+        dim3 grid((unsigned)nchunks, (unsigned)B);
+        k<<<grid, thr, smem, st>>>(c, f, f_real, seams, fp, fm.pl, (const C*)fm.tw);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     if (fp.Lg > fp.a) {
         const int64_t total = B * nchunks * (fp.Lg - fp.a);

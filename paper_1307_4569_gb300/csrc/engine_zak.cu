@@ -17,35 +17,12 @@
 // Layouts: signals [B][L]; ZF, ZG [.][d][K0] (xi-major); intermediate Y [B][J][N_sep][M_sep]
 // (one row per separable time index, k contiguous); coefficients [B][N][M] (m contiguous).
 #include "engine.h"
+#include "kcommon.cuh"
 
 #include <algorithm>
 
 namespace dgt {
 
-
-template <typename C> __device__ __forceinline__ C chirp_factor(const ChirpParams<C>& cp, int64_t l) {
-    // pchirp(L, s)(l) = exp(pi i (s l^2 (L+1) mod 2L) / L) = exp(2 pi i e / 2L)
-    const uint64_t twoL = 2 * (uint64_t)cp.L;
-    const uint64_t lr = (uint64_t)l;
-    const uint64_t l2 = (lr * lr) % twoL;
-    const uint64_t t = mulmod(l2, ((uint64_t)cp.L + 1) % twoL, twoL);
-    const uint64_t e = mulmod((uint64_t)cp.s_2L, t, twoL);
-    C w = cp.cis2L((int64_t)e);
-    if (cp.conj) w.y = -w.y;
-    return w;
-}
-
-template <typename C> __device__ __forceinline__ C load_any(const void* p, int is_real, int64_t i) {
-    using R = typename RealOf<C>::type;
-    if (is_real) return mk(reinterpret_cast<const R*>(p)[i], (R)0);
-    return reinterpret_cast<const C*>(p)[i];
-}
-
-template <typename C> __device__ __forceinline__ void store_any(void* p, int is_real, int64_t i, C v) {
-    using R = typename RealOf<C>::type;
-    if (is_real) reinterpret_cast<R*>(p)[i] = v.x;
-    else reinterpret_cast<C*>(p)[i] = v;
-}
 
 static size_t g_smem_optin = 0;
 template <typename K> static cudaError_t prep_smem(K kernel, size_t bytes) {
@@ -95,6 +72,10 @@ __global__ void __launch_bounds__(kThreadsBig) zak_fwd_kernel(const void* __rest
 template <typename T>
 cudaError_t launch_zak_fwd(const void* src, int src_real, int64_t sbs, cplx<T>* zf, int64_t zbs, int64_t L, int64_t d,
                            const FftRef& fd, const ChirpParams<cplx<T>>& pre, int64_t B, cudaStream_t st) {
+    {
+        const cudaError_t e = p2_zak_fwd<T>(src, src_real, sbs, zf, zbs, d, L / d, fd.tw, pre, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using C = cplx<T>;
     const int64_t K0 = L / d;
     const int64_t cap = tile_cap<T>();
@@ -159,6 +140,10 @@ __global__ void __launch_bounds__(kThreadsBig) prod_ifft_kernel(const cplx<T>* _
 template <typename T>
 cudaError_t launch_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T>* y, const SepGeom& g,
                              const FftRef& fd, int64_t B, cudaStream_t st) {
+    {
+        const cudaError_t e = p2_prod_ifft<T>(zf, zg, J, y, g, fd.tw, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using C = cplx<T>;
     const int64_t cap = tile_cap<T>();
     if (g.d > cap) return cudaErrorInvalidValue;
@@ -171,51 +156,6 @@ cudaError_t launch_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cp
     dim3 grid((unsigned)((g.M + W - 1) / W), (unsigned)(J * g.q), (unsigned)B);
     k<<<grid, thr, smem, st>>>(zf, zg, y, g, J, W, fd.pl, (const C*)fd.tw);
     return cudaGetLastError();
-}
-
-// =====================================================================================
-// output index map of one separable coefficient (analysis store / synthesis gather)
-// row = (b, j, n) of Y, m = channel of the separable DGT.  Returns the offset into c
-// and the phase to multiply with (analysis) -- synthesis uses its conjugate.
-// =====================================================================================
-template <typename C>
-__device__ __forceinline__ int64_t out_index(const PostParams<C>& pp, const SepGeom& g, int64_t b, int64_t j,
-                                             int64_t n, int64_t m, C& ph) {
-    ph.x = 1;
-    ph.y = 0;
-    switch (pp.mode) {
-        case POST_COSET: {
-            const uint64_t e = mulmod((uint64_t)((n * pp.at) % pp.L), (uint64_t)__ldg(pp.sigma + j), (uint64_t)pp.L);
-            ph = pp.cisL(-(int64_t)e);
-            return (b * pp.N + pp.lam2 * n + j) * pp.M + m;
-        }
-        case POST_SHEAR0: {
-            const uint64_t L = pp.L, twoN = 2 * (uint64_t)pp.N;
-            const uint64_t sa = mulmod((uint64_t)pp.s1a_modL, (uint64_t)n, L);
-            const int64_t rot = (int64_t)((L - sa) % L) / pp.b;
-            const uint64_t nn = mulmod((uint64_t)n, (uint64_t)n, twoN);
-            ph = pp.cis2N((int64_t)mulmod((uint64_t)pp.C1_2N, nn, twoN));
-            int64_t mo = m + rot;
-            if (mo >= pp.M) mo -= pp.M;
-            return (b * pp.N + n) * pp.M + mo;
-        }
-        case POST_SHEAR1: {
-            // separable channel kappa = m, separable time mr = n; Algorithm 1 index k = -kappa mod Nr
-            const uint64_t N = pp.N, twoN = 2 * N, L = pp.L;
-            const uint64_t k = (uint64_t)((pp.Nr - m) % pp.Nr);
-            const uint64_t mr = (uint64_t)n;
-            const uint64_t mt = (mulmod((uint64_t)pp.C1 % N, k % N, N) + mulmod((uint64_t)pp.C2_N, mr % N, N)) % N;
-            const uint64_t sq1 = (mulmod((uint64_t)pp.C1_2N_, k % twoN, twoN) + mulmod((uint64_t)pp.C2_2N, mr % twoN, twoN)) % twoN;
-            const uint64_t t1 = mulmod((uint64_t)pp.C3_2N, mulmod(sq1, sq1, twoN), twoN);
-            const uint64_t inner = (mulmod((uint64_t)pp.C4_2N, mr % twoN, twoN) + mulmod((uint64_t)pp.C5_2N, k % twoN, twoN)) % twoN;
-            const uint64_t t2 = mulmod(mr % twoN, inner, twoN);
-            ph = pp.cis2N((int64_t)((t1 + twoN - t2) % twoN));
-            const uint64_t kt = ((mulmod((uint64_t)pp.s1ar_L, k % L, L) + mulmod((uint64_t)pp.C6_L, mr % L, L)) % L) / (uint64_t)pp.b;
-            return (b * pp.N + (int64_t)mt) * pp.M + (int64_t)kt;
-        }
-        default:
-            return (b * g.d * g.q + n) * g.M + m;
-    }
 }
 
 // =====================================================================================
@@ -267,6 +207,10 @@ __global__ void __launch_bounds__(kThreadsBig) fft_post_kernel(const cplx<T>* __
 template <typename T>
 cudaError_t launch_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const FftRef& fm,
                             const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    {
+        const cudaError_t e = p2_fft_post<T>(y, c, g, J, fm.tw, pp, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using C = cplx<T>;
     const int64_t n = g.M;
     const int64_t cap = tile_cap<T>();
@@ -329,6 +273,10 @@ __global__ void __launch_bounds__(kThreadsBig) pre_ifft_kernel(const cplx<T>* __
 template <typename T>
 cudaError_t launch_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const FftRef& fm,
                             const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    {
+        const cudaError_t e = p2_pre_ifft<T>(c, y, g, J, fm.tw, pp, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using C = cplx<T>;
     const int64_t n = g.M;
     const int64_t cap = tile_cap<T>();
@@ -404,6 +352,10 @@ __global__ void __launch_bounds__(kThreadsBig) fft_prod_adj_kernel(const cplx<T>
 template <typename T>
 cudaError_t launch_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
                                 const FftRef& fd, int64_t B, cudaStream_t st) {
+    {
+        const cudaError_t e = p2_fft_prod_adj<T>(y, zg, J, zf, g, fd.tw, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using C = cplx<T>;
     // two work tiles d*W plus the accumulator p*d*W
     const int64_t elems = (int64_t)(kSmemBudget / sizeof(C));
@@ -524,6 +476,10 @@ __global__ void __launch_bounds__(kThreadsBig) zak_inv_kernel(const cplx<T>* __r
 template <typename T>
 cudaError_t launch_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t L, int64_t d,
                            const FftRef& fd, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st) {
+    {
+        const cudaError_t e = p2_zak_inv<T>(zf, zbs, dst, dst_real, dbs, d, L / d, fd.tw, post, scale, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using C = cplx<T>;
     const int64_t K0 = L / d;
     const int64_t cap = tile_cap<T>();

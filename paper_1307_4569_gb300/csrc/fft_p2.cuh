@@ -1,0 +1,93 @@
+// Power-of-two FFT with compile-time length N (16 <= N <= 8192), 16 values per thread.
+//
+// A transform is computed by G = N/16 threads (index t).  Stage s has radix R_s = 16, except
+// the last stage whose radix is 2^(log2 N mod 4) when that is not 0; each thread performs
+// 16/R_s butterflies j = t + G u of the stage (Stockham, self-sorting):
+//   inputs  x[j + r N/R],  twiddle exp(DIR 2 pi i r (j mod Ns)/(Ns R)),  DFT_R,
+//   outputs at (j div Ns) Ns R + (j mod Ns) + r Ns,          Ns = product of earlier radices.
+// Stage 0 reads its inputs through the caller's load(e) functor (straight from global
+// memory); the last stage leaves its outputs in registers, register u R + r holding
+// element j + r Ns (see p2_out_pos).  Between stages the values cross one shared buffer
+// whose index is padded by one element per 16 (spad), which keeps the Stockham strides
+// free of bank conflicts.  W transforms are interleaved column-wise in the buffer
+// (element e of transform c at spad(e) W + c) so that W consecutive threads serve W
+// consecutive columns of a row-major array.
+#pragma once
+#include "fft.cuh"
+
+namespace dgt {
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+__device__ __forceinline__ int spad(int e) { return e + (e >> 4); }
+
+template <int N> struct Pow2 {
+    static_assert(N >= 16 && N <= 8192 && (N & (N - 1)) == 0, "power of two in [16, 8192]");
+    static constexpr int LOG = ilog2c(N);
+    static constexpr int G = N / 16;
+    static constexpr int NST = (LOG + 3) / 4;
+    static constexpr int radix(int s) { return (s < NST - 1 || (LOG & 3) == 0) ? 16 : (1 << (LOG & 3)); }
+    static constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
+    static constexpr int RL = radix(NST - 1);          // last radix
+    static constexpr int NSL = N / RL;                 // Ns of the last stage
+    static constexpr int SMEM = N + N / 16;            // padded elements per transform
+};
+
+// element index held by register idx of thread t after the last stage
+template <int N> __device__ __forceinline__ int p2_out_pos(int t, int idx) {
+    using P = Pow2<N>;
+    const int u = idx / P::RL, r = idx % P::RL;
+    return t + P::G * u + r * P::NSL;
+}
+
+template <int N, int DIR, int W, int S, typename C>
+__device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restrict__ tw, C (&v)[16]) {
+    using P = Pow2<N>;
+    constexpr int Rp = P::radix(S - 1);
+    constexpr int Nsp = P::ns(S - 1);
+    constexpr int Bp = 16 / Rp;
+#pragma unroll
+    for (int u = 0; u < Bp; ++u) {
+        const int j = t + P::G * u;
+        const int base = (j / Nsp) * Nsp * Rp + (j % Nsp);
+#pragma unroll
+        for (int r = 0; r < Rp; ++r) sm[spad(base + r * Nsp) * W + c] = v[u * Rp + r];
+    }
+    __syncthreads();
+    constexpr int R = P::radix(S);
+    constexpr int Ns = P::ns(S);
+    constexpr int B = 16 / R;
+    constexpr int NR = N / R;
+    constexpr int TS = N / (Ns * R);
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const int j = t + P::G * u;
+        const int k = j % Ns;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            C x = sm[spad(j + r * NR) * W + c];
+            if (r > 0) {
+                C w = __ldg(tw + r * k * TS);
+                if (DIR > 0) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[u * R + r] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < B; ++u) dft_small<R, DIR>(v + u * R);
+    if constexpr (S + 1 < P::NST) p2_stages<N, DIR, W, S + 1>(c, t, sm, tw, v);
+}
+
+// Full transform: v receives the outputs (positions from p2_out_pos).  All threads of the
+// block must call it (it synchronises the block); `sm` holds Pow2<N>::SMEM * W elements.
+template <int N, int DIR, int W, typename C, class Load>
+__device__ __forceinline__ void fft_p2(int c, int t, C* sm, const C* __restrict__ tw, Load&& load, C (&v)[16]) {
+    using P = Pow2<N>;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = load(t + r * P::G);
+    dft16<DIR>(v);
+    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1>(c, t, sm, tw, v);
+}
+
+}  // namespace dgt

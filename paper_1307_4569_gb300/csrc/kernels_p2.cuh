@@ -1,0 +1,545 @@
+// Hot-path kernels for power-of-two FFT lengths (fft_p2).  Same arithmetic as the generic
+// kernels of engine_zak.cu / engine_aux.cu (see their comments for the formulas), with the
+// first FFT stage fused into the global loads and the last into the global stores.
+//
+// Column kernels transform along the strided dimension of a row-major [n][cols] array:
+// W consecutive columns share a CTA (W * N/16 threads), so every load and store instruction
+// touches W consecutive elements of a row.  Row kernels transform contiguous rows: RPB rows
+// per CTA, N/16 threads each.
+#pragma once
+#include "fft_p2.cuh"
+#include "kcommon.cuh"
+
+namespace dgt {
+
+template <typename T, int N> struct ColCfg {
+    static constexpr int G = N / 16;
+    static constexpr int WMAX = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int WT = (512 / G) < 1 ? 1 : (512 / G);                           // <= 512 threads
+    static constexpr int WS = (int)(kSmemBudget / (sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM));
+    static constexpr int W = WMAX < WT ? (WMAX < WS ? WMAX : WS) : (WT < WS ? WT : WS);  // columns per CTA
+    static constexpr int THREADS = W * G;
+    static constexpr size_t SMEM = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * W;
+    static_assert(W >= 1, "tile does not fit");
+};
+
+template <int N> struct RowCfg {
+    static constexpr int G = N / 16;
+    static constexpr int RPB = G >= 256 ? 1 : 256 / G;                   // rows per CTA
+    static constexpr int THREADS = RPB * G;
+};
+
+template <typename K> static cudaError_t p2_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------
+// zak_fwd: ZF[b][xi][col] = sum_mu x(col + K0 mu) e^{-2 pi i mu xi / d}   (d = N)
+// ------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_fwd_p2(const void* __restrict__ src, int src_real,
+                                                                    int64_t sbs, cplx<T>* __restrict__ zf,
+                                                                    int64_t zbs, int64_t K0,
+                                                                    const cplx<T>* __restrict__ tw,
+                                                                    ChirpParams<cplx<T>> pre) {
+    using C = cplx<T>;
+    using CF = ColCfg<T, N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.y;
+    const int64_t col = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = col < K0;
+    C v[16];
+    fft_p2<N, -1, CF::W>(c, t, sm, tw, [&](int e) -> C {
+        if (!ok) return mk((T)0, (T)0);
+        const int64_t l = col + K0 * e;
+        C x = load_any<C>(src, src_real, b * sbs + l);
+        if (pre.mode == PRE_CHIRP) x = cmul(x, chirp_factor(pre, l));
+        return x;
+    }, v);
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) zf[b * zbs + (int64_t)p2_out_pos<N>(t, i) * K0 + col] = v[i];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// prod_ifft (p = 1): X_w[xi][k] = ZF[xi][k] conj(ZG~_j[xi][k - a w]), inverse FFT over xi,
+// Y[b][j][w + q nu][k] = h / d.   grid (k-blocks, J q, B)
+// ------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS) prod_ifft_p2(const cplx<T>* __restrict__ zf,
+                                                                      const cplx<T>* __restrict__ zg,
+                                                                      cplx<T>* __restrict__ y, SepGeom g, int64_t J,
+                                                                      const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using CF = ColCfg<T, N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.z;
+    const int64_t j = blockIdx.y / g.q, w = blockIdx.y % g.q;
+    const int64_t k = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = k < g.M;
+    int64_t colG = k - g.a * w;
+    const bool wrap = colG < 0;
+    if (wrap) colG += g.K0;
+    const C* zfb = zf + b * g.L + k;
+    const C* zgj = zg + j * g.L + colG;
+    C v[16];
+    fft_p2<N, +1, CF::W>(c, t, sm, tw, [&](int xi) -> C {
+        if (!ok) return mk((T)0, (T)0);
+        C x = cmulc(zfb[(int64_t)xi * g.K0], zgj[(int64_t)xi * g.K0]);
+        if (wrap) x = cmulc(x, __ldg(tw + xi));
+        return x;
+    }, v);
+    if (ok) {
+        const T scale = (T)1 / (T)N;
+        C* yb = y + ((b * J + j) * g.d * g.q + w) * g.M + k;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) yb[(int64_t)g.q * p2_out_pos<N>(t, i) * g.M] = cscale(v[i], scale);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// fft_prod_adj (p = 1): for every (j, w) FFT over nu of Y'[b][j][w + q nu][k], / d, times
+// ZG~_j[xi][k - a w], summed into ZF'[b][xi][k].   grid (k-blocks, B)
+// ------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS) fft_prod_adj_p2(const cplx<T>* __restrict__ y,
+                                                                         const cplx<T>* __restrict__ zg,
+                                                                         cplx<T>* __restrict__ zf, SepGeom g,
+                                                                         int64_t J, const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using CF = ColCfg<T, N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = k < g.M;
+    const T scale = (T)1 / (T)N;
+    C acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = mk((T)0, (T)0);
+    for (int64_t j = 0; j < J; ++j) {
+        for (int64_t w = 0; w < g.q; ++w) {
+            const C* yb = y + ((b * J + j) * g.d * g.q + w) * g.M + k;
+            C v[16];
+            fft_p2<N, -1, CF::W>(c, t, sm, tw, [&](int nu) -> C {
+                return ok ? yb[(int64_t)g.q * nu * g.M] : mk((T)0, (T)0);
+            }, v);
+            int64_t colG = k - g.a * w;
+            const bool wrap = colG < 0;
+            if (wrap) colG += g.K0;
+            const C* zgj = zg + j * g.L + colG;
+            if (ok) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int xi = p2_out_pos<N>(t, i);
+                    C u = cmul(cscale(v[i], scale), zgj[(int64_t)xi * g.K0]);
+                    if (wrap) u = cmul(u, __ldg(tw + xi));
+                    acc[i] = cadd(acc[i], u);
+                }
+            }
+            __syncthreads();          // the next transform reuses the exchange buffer
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) zf[b * g.L + (int64_t)p2_out_pos<N>(t, i) * g.K0 + k] = acc[i];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// zak_inv: unnormalised inverse DFT over xi per column, post-op, store
+// ------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_inv_p2(const cplx<T>* __restrict__ zf, int64_t zbs,
+                                                                    void* __restrict__ dst, int dst_real, int64_t dbs,
+                                                                    int64_t K0, const cplx<T>* __restrict__ tw,
+                                                                    ChirpParams<cplx<T>> post, T scale) {
+    using C = cplx<T>;
+    using CF = ColCfg<T, N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.y;
+    const int64_t col = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = col < K0;
+    C v[16];
+    fft_p2<N, +1, CF::W>(c, t, sm, tw, [&](int xi) -> C {
+        return ok ? zf[b * zbs + (int64_t)xi * K0 + col] : mk((T)0, (T)0);
+    }, v);
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int64_t l = col + K0 * p2_out_pos<N>(t, i);
+            C x = cscale(v[i], scale);
+            if (post.mode == PRE_CHIRP) x = cmul(x, chirp_factor(post, l));
+            store_any(dst, dst_real, b * dbs + l, x);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// row kernels: per-row state of the route post-processing
+// ------------------------------------------------------------------------------------
+template <typename C> struct RowMap {
+    int64_t base;      // offset of output channel 0 of this row (modes with a per-row phase)
+    int64_t rot;       // cyclic rotation of the channel index (shear, s0 = 0)
+    C ph;              // per-row phase
+};
+
+template <typename C>
+__device__ __forceinline__ RowMap<C> row_map(const PostParams<C>& pp, const SepGeom& g, int64_t b, int64_t j,
+                                             int64_t nn) {
+    RowMap<C> r;
+    const int64_t o0 = out_index(pp, g, b, j, nn, 0, r.ph);
+    if (pp.mode == POST_SHEAR0) {
+        r.base = (b * pp.N + nn) * pp.M;
+        r.rot = o0 - r.base;
+    } else {
+        r.base = o0;
+        r.rot = 0;
+    }
+    return r;
+}
+
+// fft_post: FFT over k of rows of Y, route post-processing, store into c
+template <typename T, int N>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>* __restrict__ y,
+                                                                  cplx<T>* __restrict__ c, SepGeom g, int64_t J,
+                                                                  int64_t rows_total, const cplx<T>* __restrict__ tw,
+                                                                  PostParams<cplx<T>> pp) {
+    using C = cplx<T>;
+    using RC = RowCfg<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / RC::G, t = threadIdx.x % RC::G;
+    C* sm = reinterpret_cast<C*>(smem_raw) + gi * Pow2<N>::SMEM;
+    const int64_t row = (int64_t)blockIdx.x * RC::RPB + gi;
+    const bool ok = row < rows_total;
+    const C* yr = y + row * N;
+    C v[16];
+    fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
+    if (!ok) return;
+    const int64_t Nsep = g.d * g.q;
+    const int64_t b = row / (J * Nsep);
+    const int64_t rem = row - b * J * Nsep;
+    const int64_t j = rem / Nsep, nn = rem - j * Nsep;
+    if (pp.mode == POST_SHEAR1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            C ph;
+            const int64_t o = out_index(pp, g, b, j, nn, p2_out_pos<N>(t, i), ph);
+            c[o] = cmul(v[i], ph);
+        }
+    } else {
+        const RowMap<C> rm = row_map(pp, g, b, j, nn);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            int64_t m = p2_out_pos<N>(t, i) + rm.rot;
+            if (m >= N) m -= N;
+            c[rm.base + m] = cmul(v[i], rm.ph);
+        }
+    }
+}
+
+// pre_ifft: gather c with conjugate phases, unnormalised inverse FFT, store rows of Y
+template <typename T, int N>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>* __restrict__ c,
+                                                                  cplx<T>* __restrict__ y, SepGeom g, int64_t J,
+                                                                  int64_t rows_total, const cplx<T>* __restrict__ tw,
+                                                                  PostParams<cplx<T>> pp) {
+    using C = cplx<T>;
+    using RC = RowCfg<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / RC::G, t = threadIdx.x % RC::G;
+    C* sm = reinterpret_cast<C*>(smem_raw) + gi * Pow2<N>::SMEM;
+    const int64_t row = (int64_t)blockIdx.x * RC::RPB + gi;
+    const bool ok = row < rows_total;
+    const int64_t Nsep = g.d * g.q;
+    const int64_t b = ok ? row / (J * Nsep) : 0;
+    const int64_t rem = row - b * J * Nsep;
+    const int64_t j = ok ? rem / Nsep : 0, nn = ok ? rem - j * Nsep : 0;
+    RowMap<C> rm{};
+    if (ok && pp.mode != POST_SHEAR1) rm = row_map(pp, g, b, j, nn);
+    C v[16];
+    fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+        if (!ok) return mk((T)0, (T)0);
+        if (pp.mode == POST_SHEAR1) {
+            C ph;
+            const int64_t o = out_index(pp, g, b, j, nn, m, ph);
+            return cmulc(c[o], ph);
+        }
+        int64_t mo = m + rm.rot;
+        if (mo >= N) mo -= N;
+        return cmulc(c[rm.base + mo], rm.ph);
+    }, v);
+    if (!ok) return;
+    C* yr = y + row * N;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) yr[p2_out_pos<N>(t, i)] = v[i];
+}
+
+// FIR analysis: h_n(k) gathered straight from the signal, FFT over k, store column n of c
+template <typename T, int N>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void* __restrict__ f, int f_real,
+                                                                      cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
+                                                                      int64_t rows_total,
+                                                                      const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using RC = RowCfg<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / RC::G, t = threadIdx.x % RC::G;
+    C* sm = reinterpret_cast<C*>(smem_raw) + gi * Pow2<N>::SMEM;
+    const int64_t row = (int64_t)blockIdx.x * RC::RPB + gi;
+    const bool ok = row < rows_total;
+    const int64_t b = ok ? row / fp.N : 0, n = ok ? row - b * fp.N : 0;
+    const int64_t ln = fp.a * n - fp.center;
+    const int64_t wn = (n * fp.lam1) % fp.lam2;
+    const int64_t LM = fp.lam2 * fp.M;
+    C v[16];
+    fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
+        C h = mk((T)0, (T)0);
+        if (!ok) return h;
+        for (int64_t tap = posmod((int64_t)k - ln, (int64_t)N); tap < fp.Lg; tap += N) {
+            const int64_t l = posmod(ln + tap, fp.L);
+            C x = cmulc(load_any<C>(f, f_real, b * fp.L + l), __ldg(fp.taps + tap));
+            if (wn) x = cmul(x, fp.cisLM(-(int64_t)mulmod((uint64_t)(l % LM), (uint64_t)wn, (uint64_t)LM)));
+            h = cadd(h, x);
+        }
+        return h;
+    }, v);
+    if (!ok) return;
+    C* cr = c + row * N;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) cr[p2_out_pos<N>(t, i)] = v[i];
+}
+
+// FIR synthesis: inverse FFT of the chunk's columns into shared rows, then the gather of
+// the generic kernel (fir_synthesis_kernel) with the same seams.
+template <typename T, int N>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_synthesis_p2(const cplx<T>* __restrict__ c,
+                                                                       void* __restrict__ f, int f_real,
+                                                                       cplx<T>* __restrict__ seams,
+                                                                       FirParams<cplx<T>> fp,
+                                                                       const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using RC = RowCfg<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int SM = Pow2<N>::SMEM;
+    C* rows = reinterpret_cast<C*>(smem_raw);           // cols rows of SM elements (padded index)
+    const int gi = threadIdx.x / RC::G, t = threadIdx.x % RC::G;
+    const int64_t b = blockIdx.y;
+    const int64_t chunk = blockIdx.x;
+    const int64_t nchunks = gridDim.x;
+    const int64_t n0 = chunk * fp.cols;
+    const int nc = (int)fp.cols;
+    for (int r0 = 0; r0 < nc; r0 += RC::RPB) {
+        const int r = r0 + gi;
+        const bool ok = r < nc;
+        C* sm = rows + (ok ? r : nc) * SM;                  // row nc is a spare row for idle groups
+        const C* cr = c + (b * fp.N + n0 + (ok ? r : 0)) * fp.M;
+        C v[16];
+        fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C { return ok ? cr[m] : mk((T)0, (T)0); }, v);
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sm[spad(p2_out_pos<N>(t, i))] = v[i];
+        }
+        __syncthreads();
+    }
+    const int64_t S = fp.a * (nc - 1) + fp.Lg;
+    const int64_t ov = fp.Lg > fp.a ? fp.Lg - fp.a : 0;
+    const int64_t lstart = fp.a * n0 - fp.center;
+    const int64_t LM = fp.lam2 * fp.M;
+    C* seamL = seams + (b * nchunks + chunk) * 2 * ov;
+    C* seamR = seamL + ov;
+    for (int64_t tt = threadIdx.x; tt < S; tt += blockDim.x) {
+        const int64_t l = posmod(lstart + tt, fp.L);
+        const int km = (int)(l % N);
+        C acc = mk((T)0, (T)0);
+        const int64_t rlo = tt - fp.Lg + 1 <= 0 ? 0 : (tt - fp.Lg + fp.a) / fp.a;
+        const int64_t rhi = min((int64_t)nc - 1, tt / fp.a);
+        for (int64_t r = rlo; r <= rhi; ++r) {
+            const int64_t tap = tt - fp.a * r;
+            const int64_t n = n0 + r;
+            const int64_t wn = (n * fp.lam1) % fp.lam2;
+            C x = cmul(rows[r * SM + spad(km)], __ldg(fp.taps + tap));
+            if (wn) x = cmul(x, fp.cisLM((int64_t)mulmod((uint64_t)(l % LM), (uint64_t)wn, (uint64_t)LM)));
+            acc = cadd(acc, x);
+        }
+        if (tt < ov) seamL[tt] = acc;
+        else if (tt >= S - ov) seamR[tt - (S - ov)] = acc;
+        else store_any(f, f_real, b * fp.L + l, acc);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// launchers (N dispatched at run time)
+// ------------------------------------------------------------------------------------
+#define P2_SWITCH(NV, CALL)                    \
+    switch (NV) {                              \
+        case 128: { constexpr int NN = 128; CALL; } \
+        case 256: { constexpr int NN = 256; CALL; } \
+        case 512: { constexpr int NN = 512; CALL; } \
+        case 1024: { constexpr int NN = 1024; CALL; } \
+        case 2048: { constexpr int NN = 2048; CALL; } \
+        case 4096: { constexpr int NN = 4096; CALL; } \
+        case 8192: { constexpr int NN = 8192; CALL; } \
+        default: return cudaErrorNotSupported;  \
+    }
+
+inline bool p2_len_ok(int64_t n) { return n >= 128 && n <= 8192 && (n & (n - 1)) == 0; }
+
+template <typename T, int N>
+cudaError_t p2_zak_fwd_n(const void* src, int src_real, int64_t sbs, cplx<T>* zf, int64_t zbs, int64_t K0,
+                         const void* tw, const ChirpParams<cplx<T>>& pre, int64_t B, cudaStream_t st) {
+    using CF = ColCfg<T, N>;
+    auto k = zak_fwd_p2<T, N>;
+    cudaError_t e = p2_smem(k, CF::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((K0 + CF::W - 1) / CF::W), (unsigned)B);
+    k<<<grid, CF::THREADS, CF::SMEM, st>>>(src, src_real, sbs, zf, zbs, K0, (const cplx<T>*)tw, pre);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t p2_prod_ifft_n(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T>* y, const SepGeom& g,
+                           const void* tw, int64_t B, cudaStream_t st) {
+    using CF = ColCfg<T, N>;
+    auto k = prod_ifft_p2<T, N>;
+    cudaError_t e = p2_smem(k, CF::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.M + CF::W - 1) / CF::W), (unsigned)(J * g.q), (unsigned)B);
+    k<<<grid, CF::THREADS, CF::SMEM, st>>>(zf, zg, y, g, J, (const cplx<T>*)tw);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t p2_fft_prod_adj_n(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
+                              const void* tw, int64_t B, cudaStream_t st) {
+    using CF = ColCfg<T, N>;
+    auto k = fft_prod_adj_p2<T, N>;
+    cudaError_t e = p2_smem(k, CF::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.M + CF::W - 1) / CF::W), (unsigned)B);
+    k<<<grid, CF::THREADS, CF::SMEM, st>>>(y, zg, zf, g, J, (const cplx<T>*)tw);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t p2_zak_inv_n(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t K0,
+                         const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st) {
+    using CF = ColCfg<T, N>;
+    auto k = zak_inv_p2<T, N>;
+    cudaError_t e = p2_smem(k, CF::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((K0 + CF::W - 1) / CF::W), (unsigned)B);
+    k<<<grid, CF::THREADS, CF::SMEM, st>>>(zf, zbs, dst, dst_real, dbs, K0, (const cplx<T>*)tw, post, scale);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t p2_fft_post_n(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const void* tw,
+                          const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    using RC = RowCfg<N>;
+    const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
+    auto k = fft_post_p2<T, N>;
+    cudaError_t e = p2_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t rows = B * J * g.d * g.q;
+    k<<<(unsigned)((rows + RC::RPB - 1) / RC::RPB), RC::THREADS, smem, st>>>(y, c, g, J, rows, (const cplx<T>*)tw, pp);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t p2_pre_ifft_n(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const void* tw,
+                          const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    using RC = RowCfg<N>;
+    const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
+    auto k = pre_ifft_p2<T, N>;
+    cudaError_t e = p2_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t rows = B * J * g.d * g.q;
+    k<<<(unsigned)((rows + RC::RPB - 1) / RC::RPB), RC::THREADS, smem, st>>>(c, y, g, J, rows, (const cplx<T>*)tw, pp);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t p2_fir_analysis_n(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp, const void* tw,
+                              int64_t B, cudaStream_t st) {
+    using RC = RowCfg<N>;
+    const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
+    auto k = fir_analysis_p2<T, N>;
+    cudaError_t e = p2_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t rows = B * fp.N;
+    k<<<(unsigned)((rows + RC::RPB - 1) / RC::RPB), RC::THREADS, smem, st>>>(f, f_real, c, fp, rows,
+                                                                            (const cplx<T>*)tw);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t p2_fir_synthesis_n(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
+                               const void* tw, int64_t B, cudaStream_t st) {
+    using RC = RowCfg<N>;
+    const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * (fp.cols + 1);
+    if (smem > kSmemBudget + 16 * 1024) return cudaErrorNotSupported;
+    auto k = fir_synthesis_p2<T, N>;
+    cudaError_t e = p2_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(fp.N / fp.cols), (unsigned)B);
+    k<<<grid, RC::THREADS, smem, st>>>(c, f, f_real, seams, fp, (const cplx<T>*)tw);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// run-time dispatch over the instantiated lengths; cudaErrorNotSupported = use the generic path
+// ------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t p2_zak_fwd(const void* src, int src_real, int64_t sbs, cplx<T>* zf, int64_t zbs, int64_t d, int64_t K0,
+                       const void* tw, const ChirpParams<cplx<T>>& pre, int64_t B, cudaStream_t st) {
+    P2_SWITCH(d, return (p2_zak_fwd_n<T, NN>(src, src_real, sbs, zf, zbs, K0, tw, pre, B, st)))
+}
+template <typename T>
+cudaError_t p2_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T>* y, const SepGeom& g, const void* tw,
+                         int64_t B, cudaStream_t st) {
+    if (g.p != 1) return cudaErrorNotSupported;
+    P2_SWITCH(g.d, return (p2_prod_ifft_n<T, NN>(zf, zg, J, y, g, tw, B, st)))
+}
+template <typename T>
+cudaError_t p2_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
+                            const void* tw, int64_t B, cudaStream_t st) {
+    if (g.p != 1) return cudaErrorNotSupported;
+    P2_SWITCH(g.d, return (p2_fft_prod_adj_n<T, NN>(y, zg, J, zf, g, tw, B, st)))
+}
+template <typename T>
+cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
+                       const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st) {
+    P2_SWITCH(d, return (p2_zak_inv_n<T, NN>(zf, zbs, dst, dst_real, dbs, K0, tw, post, scale, B, st)))
+}
+template <typename T>
+cudaError_t p2_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const void* tw,
+                        const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    P2_SWITCH(g.M, return (p2_fft_post_n<T, NN>(y, c, g, J, tw, pp, B, st)))
+}
+template <typename T>
+cudaError_t p2_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const void* tw,
+                        const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    P2_SWITCH(g.M, return (p2_pre_ifft_n<T, NN>(c, y, g, J, tw, pp, B, st)))
+}
+template <typename T>
+cudaError_t p2_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp, const void* tw,
+                            int64_t B, cudaStream_t st) {
+    P2_SWITCH(fp.M, return (p2_fir_analysis_n<T, NN>(f, f_real, c, fp, tw, B, st)))
+}
+template <typename T>
+cudaError_t p2_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
+                             const void* tw, int64_t B, cudaStream_t st) {
+    P2_SWITCH(fp.M, return (p2_fir_synthesis_n<T, NN>(c, f, f_real, seams, fp, tw, B, st)))
+}
+
+}  // namespace dgt
