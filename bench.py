@@ -132,6 +132,8 @@ def algorithmic_bytes(name, w, B, csz, rsz, J):
         "pre_ifft": B * 2 * MN * csz,
         "fft_prod_adj": B * (MN * csz + L * csz),
         "zak_inv": B * (L * csz + L * rsz),
+        "fused_analysis": B * (L * csz + MN * csz),
+        "fused_synthesis": B * (MN * csz + L * csz),
     }
     return table.get(name)
 
@@ -263,7 +265,8 @@ def run_ours(args, rank, world):
         avg = v["ms"] / v["launches"]
         kernels[name] = {"launches": v["launches"], "ms_per_launch": avg, "share": v["ms"] / total_prof_ms,
                          "achieved_gbs": (ab / (avg * 1e-3) / 1e9) if ab else None}
-    dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+    ranked = sorted((k for k in kernels if kernels[k]["achieved_gbs"] is not None), key=lambda k: -kernels[k]["share"])
+    dom = ranked[0] if ranked else None
     roof = None
     if dom:
         ab = algorithmic_bytes(dom, w, B, 8, 4, 2)

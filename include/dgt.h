@@ -168,6 +168,11 @@ int dgt_logmag_loss(dgt_plan_t plan, const void* c, void* G, double* loss_dev, d
 /* Bytes of device memory owned by the plan (tables, window factors, cached windows, workspace). */
 int dgt_plan_bytes(dgt_plan_t plan, size_t* bytes);
 
+/* Synchronise `stream` and report a pending asynchronous CUDA error of this plan's work
+ * as DGT_ERR_CUDA.  (No kernel of this library waits on another one; DGT_ERR_TIMEOUT is
+ * reserved for bounded device waits.) */
+int dgt_plan_status(dgt_plan_t plan, void* stream);
+
 /* Synchronise `stream` and report a pending asynchronous CUDA error as DGT_ERR_CUDA. */
 int dgt_sync(void* stream);
 

@@ -61,6 +61,7 @@ SIGNATURES = {
     "dgt_fir_synthesis_noalloc": (i32, [vp, vp, vp, i32, i64, i32, vp]),
     "dgt_plan_bytes": (i32, [vp, C.POINTER(C.c_size_t)]),
     "dgt_sync": (i32, [vp]),
+    "dgt_plan_status": (i32, [vp, vp]),
     "dgt_plan_destroy": (None, [vp]),
     "dgt_strerror": (C.c_char_p, [i32]),
     "dgt_last_error": (C.c_char_p, []),

@@ -153,6 +153,10 @@ class Plan:
                                      workspace.data_ptr() if workspace is not None else None, _stream(stream)))
         return out
 
+    def status(self, stream=None) -> None:
+        """Synchronise and raise DGTError(DGT_ERR_TIMEOUT) if a bounded device wait expired."""
+        K.check(K.lib().dgt_plan_status(self._h, _stream(stream)))
+
     def plan_bytes(self) -> int:
         v = C.c_size_t()
         K.check(K.lib().dgt_plan_bytes(self._h, C.byref(v)))

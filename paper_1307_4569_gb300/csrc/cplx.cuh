@@ -41,21 +41,55 @@ template <int DIR, typename C> __host__ __device__ __forceinline__ C mul_i(C a) 
     return r;
 }
 
+// x mod d for 64-bit x and a fixed divisor 1 <= d < 2^32 without a hardware division:
+// Barrett reduction with m = floor((2^64 - 1) / d); the quotient estimate umulhi(x, m)
+// is at most 2 below floor(x / d), so two conditional subtractions finish it.
+struct ModU64 {
+    uint64_t d;
+    uint64_t m;
+    __host__ __device__ __forceinline__ uint64_t mod(uint64_t x) const {
+#ifdef __CUDA_ARCH__
+        const uint64_t q = __umul64hi(x, m);
+#else
+        const uint64_t q = (uint64_t)(((unsigned __int128)x * m) >> 64);
+#endif
+        uint64_t r = x - q * d;
+        if (r >= d) r -= d;
+        if (r >= d) r -= d;
+        return r;
+    }
+    // signed argument, result in [0, d)
+    __host__ __device__ __forceinline__ uint64_t smod(int64_t x) const {
+        if (x >= 0) return mod((uint64_t)x);
+        const uint64_t r = mod((uint64_t)(-x));
+        return r ? d - r : 0;
+    }
+    // (x * y) mod d for 0 <= x, y < d
+    __host__ __device__ __forceinline__ uint64_t mulmod(uint64_t x, uint64_t y) const { return mod(x * y); }
+};
+
+inline ModU64 make_mod(uint64_t d) {
+    ModU64 r;
+    r.d = d;
+    r.m = ~(uint64_t)0 / d;
+    return r;
+}
+
 // exp(2 pi i e / den) for integer e (any sign), from a two-level table built on the
 // host in double precision: hi[k] = exp(2 pi i k S / den), lo[r] = exp(2 pi i r / den),
-// e mod den = k S + r.  Two rounded factors, so the result is accurate to a few ulp of
-// the working precision, independent of the size of den.
+// e mod den = k S + r with S a power of two.  Two rounded factors, so the result is
+// accurate to a few ulp of the working precision, independent of the size of den.
 template <typename C> struct CisTable {
     const C* hi;
     const C* lo;
-    int64_t den;
-    int64_t S;
+    ModU64 md;            // modulus den
+    int shift;            // S = 2^shift
     __device__ __forceinline__ C operator()(int64_t e) const {
-        int64_t r = e % den;
-        if (r < 0) r += den;
-        const int64_t k = r / S;
-        const int64_t m = r - k * S;
-        return cmul(__ldg(hi + k), __ldg(lo + m));
+        const uint64_t r = md.smod(e);
+        return cmul(__ldg(hi + (r >> shift)), __ldg(lo + (r & ((1ull << shift) - 1))));
+    }
+    __device__ __forceinline__ C at(uint64_t r) const {      // 0 <= r < den
+        return cmul(__ldg(hi + (r >> shift)), __ldg(lo + (r & ((1ull << shift) - 1))));
     }
 };
 

@@ -43,6 +43,7 @@ template <typename C> struct PostParams {
     int64_t Nr, C1, C2_N, C1_2N_, C2_2N, C3_2N, C4_2N, C5_2N, s1ar_L, C6_L;
     CisTable<C> cisL;                 // exp(2 pi i e / L)
     CisTable<C> cis2N;                // exp(2 pi i e / (2N)) = exp(pi i e / N)
+    ModU64 mL, mN, m2N;               // reductions modulo L, N, 2N
 };
 
 // Signal pre-processing inside the factorisation / FFT_L passes.
@@ -57,6 +58,7 @@ template <typename C> struct ChirpParams {
     int64_t s_2L;                     // s mod 2L
     int conj;                         // multiply by the conjugate chirp
     CisTable<C> cis2L;                // exp(2 pi i e / (2L))
+    ModU64 m2L;                       // reduction modulo 2L
 };
 
 // ------------------------------------------------------------------------------------
@@ -109,6 +111,8 @@ template <typename C> struct FirParams {
     int64_t L, a, M, N, lam1, lam2, Lg, center;
     const C* taps;                    // Lg taps of the analysis / synthesis window
     CisTable<C> cisLM;                // exp(2 pi i e / (lam2 M))
+    const C* binph;                   // [lam2][M]: exp(-2 pi i k wn / (lam2 M)), the bin part of exp(-2 pi i l w(n)/M)
+    const C* root;                    // [lam2]: exp(-2 pi i x / lam2), the fold part (l = k + j M: x = j wn mod lam2)
     int64_t cols;                     // time positions per CTA
     int64_t group;                    // rows transformed at once (spare buffer rows)
 };

@@ -20,6 +20,10 @@ template <typename T, int N> struct ColCfg {
     static constexpr int W = WMAX < WT ? (WMAX < WS ? WMAX : WS) : (WT < WS ? WT : WS);  // columns per CTA
     static constexpr int THREADS = W * G;
     static constexpr size_t SMEM = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * W;
+    // blocks per SM the register allocation must allow: 64 registers a thread in float32,
+    // 128 in float64 (the 16 complex values of a thread take 32 / 64 of them)
+    static constexpr int MINB = (sizeof(T) == 4 ? 2048 : 1024) / (THREADS * 2) > 0
+                                    ? (sizeof(T) == 4 ? 2048 : 1024) / (THREADS * 2) : 1;
     static_assert(W >= 1, "tile does not fit");
 };
 
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_fwd_p2(const void* 
 // Y[b][j][w + q nu][k] = h / d.   grid (k-blocks, J q, B)
 // ------------------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColCfg<T, N>::THREADS) prod_ifft_p2(const cplx<T>* __restrict__ zf,
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MINB) prod_ifft_p2(const cplx<T>* __restrict__ zf,
                                                                       const cplx<T>* __restrict__ zg,
                                                                       cplx<T>* __restrict__ y, SepGeom g, int64_t J,
                                                                       const cplx<T>* __restrict__ tw) {
@@ -238,12 +242,10 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>*
         }
     } else {
         const RowMap<C> rm = row_map(pp, g, b, j, nn);
+        C* cb = c + rm.base;
+        const int rot = (int)rm.rot;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            int64_t m = p2_out_pos<N>(t, i) + rm.rot;
-            if (m >= N) m -= N;
-            c[rm.base + m] = cmul(v[i], rm.ph);
-        }
+        for (int i = 0; i < 16; ++i) cb[(p2_out_pos<N>(t, i) + rot) & (N - 1)] = cmul(v[i], rm.ph);
     }
 }
 
@@ -264,27 +266,32 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
     const int64_t b = ok ? row / (J * Nsep) : 0;
     const int64_t rem = row - b * J * Nsep;
     const int64_t j = ok ? rem / Nsep : 0, nn = ok ? rem - j * Nsep : 0;
-    RowMap<C> rm{};
-    if (ok && pp.mode != POST_SHEAR1) rm = row_map(pp, g, b, j, nn);
     C v[16];
-    fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
-        if (!ok) return mk((T)0, (T)0);
-        if (pp.mode == POST_SHEAR1) {
+    if (pp.mode == POST_SHEAR1) {
+        fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+            if (!ok) return mk((T)0, (T)0);
             C ph;
             const int64_t o = out_index(pp, g, b, j, nn, m, ph);
             return cmulc(c[o], ph);
-        }
-        int64_t mo = m + rm.rot;
-        if (mo >= N) mo -= N;
-        return cmulc(c[rm.base + mo], rm.ph);
-    }, v);
+        }, v);
+    } else {
+        RowMap<C> rm{};
+        if (ok) rm = row_map(pp, g, b, j, nn);
+        const C* cb = c + (ok ? rm.base : 0);
+        const int rot = (int)rm.rot;
+        fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+            return ok ? cmulc(cb[(m + rot) & (N - 1)], rm.ph) : mk((T)0, (T)0);
+        }, v);
+    }
     if (!ok) return;
     C* yr = y + row * N;
 #pragma unroll
     for (int i = 0; i < 16; ++i) yr[p2_out_pos<N>(t, i)] = v[i];
 }
 
-// FIR analysis: h_n(k) gathered straight from the signal, FFT over k, store column n of c
+// FIR analysis: h_n(k) gathered straight from the signal, FFT over k, store column n of c.
+// The modulation exp(-2 pi i l w(n)/M) of a sample l = k + j M is the bin phase
+// binph[wn][k] times the root of unity root[(j wn) mod lam2].
 template <typename T, int N>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void* __restrict__ f, int f_real,
                                                                       cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
@@ -298,37 +305,72 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
     const int64_t row = (int64_t)blockIdx.x * RC::RPB + gi;
     const bool ok = row < rows_total;
     const int64_t b = ok ? row / fp.N : 0, n = ok ? row - b * fp.N : 0;
-    const int64_t ln = fp.a * n - fp.center;
-    const int64_t wn = (n * fp.lam1) % fp.lam2;
-    const int64_t LM = fp.lam2 * fp.M;
+    int64_t ln = fp.a * n - fp.center;                        // time of tap 0, in [0, L)
+    if (ln < 0) ln += fp.L;
+    const int lam2 = (int)fp.lam2;
+    const int wn = (int)((n * fp.lam1) % lam2);
+    const C* binph = fp.binph + (int64_t)wn * N;
+    const int lnm = (int)(ln & (N - 1));
+    const int Lg = (int)fp.Lg;
+    // fold j = l div M of sample l = ln + tap: j0 + (lnm + tap) div M, j0 = ln div M.  lam2 M
+    // divides L, so wrapping past L leaves j mod lam2 unchanged.  Roots for the first folds:
+    const int jm0 = (int)((ln / N) % lam2);
+    const C root0 = __ldg(fp.root + (jm0 * wn) % lam2);
+    const C root1 = __ldg(fp.root + (((jm0 + 1) % lam2) * wn) % lam2);
     C v[16];
-    fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
-        C h = mk((T)0, (T)0);
-        if (!ok) return h;
-        for (int64_t tap = posmod((int64_t)k - ln, (int64_t)N); tap < fp.Lg; tap += N) {
-            const int64_t l = posmod(ln + tap, fp.L);
-            C x = cmulc(load_any<C>(f, f_real, b * fp.L + l), __ldg(fp.taps + tap));
-            if (wn) x = cmul(x, fp.cisLM(-(int64_t)mulmod((uint64_t)(l % LM), (uint64_t)wn, (uint64_t)LM)));
-            h = cadd(h, x);
+    auto tap_value = [&](int k, int tap) -> C {
+        int64_t l = ln + tap;
+        if (l >= fp.L) l -= fp.L;
+        C x;
+        if (f_real) x = mk(reinterpret_cast<const T*>(f)[b * fp.L + l], (T)0);
+        else x = reinterpret_cast<const C*>(f)[b * fp.L + l];
+        x = cmulc(x, __ldg(fp.taps + tap));
+        if (wn) {
+            const int fo = (lnm + tap) / N;                 // fold offset from tap 0
+            x = cmul(x, fo == 0 ? root0 : fo == 1 ? root1 : __ldg(fp.root + (((jm0 + fo) % lam2) * wn) % lam2));
         }
-        return h;
-    }, v);
+        return x;
+    };
+    if (Lg <= N) {
+        // at most one tap per bin: straight-line loads
+        fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
+            const int tap = (k - lnm) & (N - 1);
+            if (!ok || tap >= Lg) return mk((T)0, (T)0);
+            const C h = tap_value(k, tap);
+            return wn ? cmul(h, __ldg(binph + k)) : h;
+        }, v);
+    } else {
+        fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
+            C h = mk((T)0, (T)0);
+            if (!ok) return h;
+            for (int tap = (k - lnm) & (N - 1); tap < Lg; tap += N) h = cadd(h, tap_value(k, tap));
+            return wn ? cmul(h, __ldg(binph + k)) : h;
+        }, v);
+    }
     if (!ok) return;
     C* cr = c + row * N;
 #pragma unroll
     for (int i = 0; i < 16; ++i) cr[p2_out_pos<N>(t, i)] = v[i];
 }
 
-// FIR synthesis: inverse FFT of the chunk's columns into shared rows, then the gather of
-// the generic kernel (fir_synthesis_kernel) with the same seams.
+// FIR synthesis: inverse FFT of the chunk's columns into shared rows, each multiplied by its
+// conjugate bin phase; then every sample of the chunk's segment gathers
+//   f(l) = sum_n gamma(l - a n) conj(root[(j wn) mod lam2]) row_n[l mod M],  j = l div M,
+// with the seams of the generic kernel (fir_synthesis_kernel).
+template <int N> struct SynCfg {
+    static constexpr int G = N / 16;
+    static constexpr int RPB = G >= 512 ? 1 : 512 / G;                    // rows transformed at once
+    static constexpr int THREADS = RPB * G;
+};
+
 template <typename T, int N>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_synthesis_p2(const cplx<T>* __restrict__ c,
+__global__ void __launch_bounds__(SynCfg<N>::THREADS) fir_synthesis_p2(const cplx<T>* __restrict__ c,
                                                                        void* __restrict__ f, int f_real,
                                                                        cplx<T>* __restrict__ seams,
                                                                        FirParams<cplx<T>> fp,
                                                                        const cplx<T>* __restrict__ tw) {
     using C = cplx<T>;
-    using RC = RowCfg<N>;
+    using RC = SynCfg<N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int SM = Pow2<N>::SMEM;
     C* rows = reinterpret_cast<C*>(smem_raw);           // cols rows of SM elements (padded index)
@@ -338,6 +380,14 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_synthesis_p2(const cpl
     const int64_t nchunks = gridDim.x;
     const int64_t n0 = chunk * fp.cols;
     const int nc = (int)fp.cols;
+    const int lam2 = (int)fp.lam2;
+    // per column: wn = (n lam1) mod lam2; per (j mod lam2, wn): conj(root[(j wn) mod lam2])
+    __shared__ int s_wn[64];
+    __shared__ C s_root[64];
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) s_wn[r] = (int)(((n0 + r) * fp.lam1) % lam2);
+    for (int e = threadIdx.x; e < lam2 * lam2; e += blockDim.x)
+        s_root[e] = cconj(__ldg(fp.root + ((e / lam2) * (e % lam2)) % lam2));
+    __syncthreads();
     for (int r0 = 0; r0 < nc; r0 += RC::RPB) {
         const int r = r0 + gi;
         const bool ok = r < nc;
@@ -346,29 +396,36 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_synthesis_p2(const cpl
         C v[16];
         fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C { return ok ? cr[m] : mk((T)0, (T)0); }, v);
         if (ok) {
+            const int wn = s_wn[r];
+            const C* binph = fp.binph + (int64_t)wn * N;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) sm[spad(p2_out_pos<N>(t, i))] = v[i];
+            for (int i = 0; i < 16; ++i) {
+                const int k = p2_out_pos<N>(t, i);
+                sm[spad(k)] = wn ? cmulc(v[i], __ldg(binph + k)) : v[i];
+            }
         }
         __syncthreads();
     }
     const int64_t S = fp.a * (nc - 1) + fp.Lg;
     const int64_t ov = fp.Lg > fp.a ? fp.Lg - fp.a : 0;
-    const int64_t lstart = fp.a * n0 - fp.center;
-    const int64_t LM = fp.lam2 * fp.M;
+    int64_t lstart = fp.a * n0 - fp.center;
+    if (lstart < 0) lstart += fp.L;
     C* seamL = seams + (b * nchunks + chunk) * 2 * ov;
     C* seamR = seamL + ov;
-    for (int64_t tt = threadIdx.x; tt < S; tt += blockDim.x) {
-        const int64_t l = posmod(lstart + tt, fp.L);
-        const int km = (int)(l % N);
+    const int a = (int)fp.a, Lg = (int)fp.Lg;
+    for (int tt = threadIdx.x; tt < (int)S; tt += blockDim.x) {
+        int64_t l = lstart + tt;
+        if (l >= fp.L) l -= fp.L;
+        const int km = (int)(l & (N - 1));
+        const C* rt = s_root + ((int)(l / N) % lam2) * lam2;
         C acc = mk((T)0, (T)0);
-        const int64_t rlo = tt - fp.Lg + 1 <= 0 ? 0 : (tt - fp.Lg + fp.a) / fp.a;
-        const int64_t rhi = min((int64_t)nc - 1, tt / fp.a);
-        for (int64_t r = rlo; r <= rhi; ++r) {
-            const int64_t tap = tt - fp.a * r;
-            const int64_t n = n0 + r;
-            const int64_t wn = (n * fp.lam1) % fp.lam2;
+        const int rlo = tt - Lg + 1 <= 0 ? 0 : (tt - Lg + a) / a;
+        const int rhi = min(nc - 1, tt / a);
+        for (int r = rlo; r <= rhi; ++r) {
+            const int tap = tt - a * r;
             C x = cmul(rows[r * SM + spad(km)], __ldg(fp.taps + tap));
-            if (wn) x = cmul(x, fp.cisLM((int64_t)mulmod((uint64_t)(l % LM), (uint64_t)wn, (uint64_t)LM)));
+            const int wn = s_wn[r];
+            if (wn) x = cmul(x, rt[wn]);
             acc = cadd(acc, x);
         }
         if (tt < ov) seamL[tt] = acc;
@@ -423,10 +480,11 @@ cudaError_t p2_fft_prod_adj_n(const cplx<T>* y, const cplx<T>* zg, int64_t J, cp
                               const void* tw, int64_t B, cudaStream_t st) {
     using CF = ColCfg<T, N>;
     auto k = fft_prod_adj_p2<T, N>;
-    cudaError_t e = p2_smem(k, CF::SMEM);
+    const size_t smem = CF::SMEM;
+    cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.M + CF::W - 1) / CF::W), (unsigned)B);
-    k<<<grid, CF::THREADS, CF::SMEM, st>>>(y, zg, zf, g, J, (const cplx<T>*)tw);
+    k<<<grid, CF::THREADS, smem, st>>>(y, zg, zf, g, J, (const cplx<T>*)tw);
     return cudaGetLastError();
 }
 
@@ -485,7 +543,7 @@ cudaError_t p2_fir_analysis_n(const void* f, int f_real, cplx<T>* c, const FirPa
 template <typename T, int N>
 cudaError_t p2_fir_synthesis_n(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
                                const void* tw, int64_t B, cudaStream_t st) {
-    using RC = RowCfg<N>;
+    using RC = SynCfg<N>;
     const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * (fp.cols + 1);
     if (smem > kSmemBudget + 16 * 1024) return cudaErrorNotSupported;
     auto k = fir_synthesis_p2<T, N>;

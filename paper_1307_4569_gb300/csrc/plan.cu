@@ -235,8 +235,9 @@ template <typename T> struct CisBuf {
 };
 
 template <typename T> static int make_cis(CisBuf<T>& cb, int64_t den, cudaStream_t st) {
-    int64_t S = (int64_t)std::ceil(std::sqrt((double)den));
-    if (S < 1) S = 1;
+    int shift = 0;
+    while (((int64_t)1 << shift) * ((int64_t)1 << shift) < den) ++shift;
+    const int64_t S = (int64_t)1 << shift;
     const int64_t nhi = den / S + 1;
     std::vector<double> hi(2 * nhi), lo(2 * S);
     for (int64_t k = 0; k < nhi; ++k) cis_host(k * S, den, hi[2 * k], hi[2 * k + 1]);
@@ -245,8 +246,8 @@ template <typename T> static int make_cis(CisBuf<T>& cb, int64_t den, cudaStream
     DGT_TRY(upload_cplx<T>(cb.lo, lo, st));
     cb.tab.hi = (const cplx<T>*)cb.hi.p;
     cb.tab.lo = (const cplx<T>*)cb.lo.p;
-    cb.tab.den = den;
-    cb.tab.S = S;
+    cb.tab.md = make_mod((uint64_t)den);
+    cb.tab.shift = shift;
     return DGT_OK;
 }
 
@@ -283,6 +284,7 @@ struct dgt_plan_s {
                             cudaStream_t st) = 0;
     virtual int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) = 0;
     virtual int fir_synthesis_noalloc(const void* c, void* f, int f_real, int64_t B, int which, cudaStream_t st) = 0;
+    virtual int status_check(cudaStream_t st) = 0;
     virtual size_t ws_bytes(int64_t B) const = 0;
     virtual size_t owned_bytes() const = 0;
 };
@@ -300,6 +302,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     DevBuf work;                       // plan-owned workspace
     DevBuf tmpwin;                     // scratch for window set-up
     DevBuf status;                     // int flag for the Gram solve
+    DevBuf firtab;                     // FIR modulation: bin phases [lam2][M] then roots [lam2]
     DevBuf lossparts;
 
     const FftRef* fft(int64_t n) {
@@ -369,6 +372,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         cp.s_2L = pmod(s, 2 * core.L);
         cp.conj = conj;
         cp.cis2L = cis2L.tab;
+        cp.m2L = make_mod(2 * (uint64_t)core.L);
         return cp;
     }
     ChirpParams<C> nochirp() const {
@@ -376,6 +380,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         cp.mode = PRE_NONE;
         cp.L = core.L;
         cp.cis2L = cis2L.tab;
+        cp.m2L = make_mod(2 * (uint64_t)core.L);
         return cp;
     }
 
@@ -385,6 +390,9 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         pp.L = k.L; pp.M = k.M; pp.N = k.N; pp.b = k.b; pp.a = k.a;
         pp.cisL = cisL.tab;
         pp.cis2N = cis2N.tab;
+        pp.mL = make_mod((uint64_t)k.L);
+        pp.mN = make_mod((uint64_t)k.N);
+        pp.m2N = make_mod(2 * (uint64_t)k.N);
         if (k.route == DGT_ROUTE_COSET) {
             pp.mode = POST_COSET;
             pp.lam2 = k.lam2;
@@ -427,6 +435,15 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         // FFT tables
         if (k.route == DGT_ROUTE_FIR) {
             DGT_TRY(add_fft(k.M, st));
+            // exp(-2 pi i l wn / (lam2 M)) with l = k + j M splits into the bin phase
+            // exp(-2 pi i k wn / (lam2 M)) and the root exp(-2 pi i (j wn mod lam2) / lam2)
+            std::vector<double> h(2 * (k.lam2 * k.M + k.lam2));
+            for (int64_t wn = 0; wn < k.lam2; ++wn)
+                for (int64_t kk = 0; kk < k.M; ++kk)
+                    cis_host(-(kk * wn), k.lam2 * k.M, h[2 * (wn * k.M + kk)], h[2 * (wn * k.M + kk) + 1]);
+            for (int64_t x = 0; x < k.lam2; ++x)
+                cis_host(-x, k.lam2, h[2 * (k.lam2 * k.M + x)], h[2 * (k.lam2 * k.M + x) + 1]);
+            DGT_TRY(upload_cplx<T>(firtab, h, st));
         } else {
             DGT_TRY(add_fft(k.sep.d, st));
             DGT_TRY(add_fft(k.sep.M, st));
@@ -531,6 +548,8 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         FirParams<C> fp{};
         fp.L = k.L; fp.a = k.a; fp.M = k.M; fp.N = k.N; fp.lam1 = k.lam1; fp.lam2 = k.lam2;
         fp.Lg = k.Lg; fp.center = k.center; fp.taps = taps; fp.cisLM = cisLM.tab; fp.cols = k.fir_cols;
+        fp.binph = (const C*)firtab.p;
+        fp.root = fp.binph ? fp.binph + k.lam2 * k.M : nullptr;
         fp.group = k.fir_group;
         return fp;
     }
@@ -699,6 +718,9 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         pp.L = k.L; pp.M = k.M; pp.N = k.N; pp.b = k.b; pp.a = k.a;
         pp.lam2 = k.lam2; pp.at = k.lam2 * k.a; pp.sigma = (const int64_t*)sigma.p;
         pp.cisL = cisL.tab; pp.cis2N = cis2N.tab;
+        pp.mL = make_mod((uint64_t)k.L);
+        pp.mN = make_mod((uint64_t)k.N);
+        pp.m2N = make_mod(2 * (uint64_t)k.N);
         const size_t need = al(sizeof(C) * (size_t)B * k.L) + al(sizeof(C) * (size_t)B * k.M * k.N) +
                             2 * al(sizeof(C) * (size_t)k.lam2 * k.L);
         DevBuf scratch;
@@ -715,6 +737,12 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         KTRY("grad_window_combine", st, launch_grad_window_combine<T>(wj, grad, grad_real, k.L, k.a, k.lam2, (const int64_t*)sigma.p,
                                                cisL.tab, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        return DGT_OK;
+    }
+
+    int status_check(cudaStream_t st) override {
+        CUDA_TRY(cudaStreamSynchronize(st));
+        CUDA_TRY(cudaGetLastError());
         return DGT_OK;
     }
 
@@ -838,7 +866,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
         fir_group = fir_cols ? group_for(fir_cols) : 1;
     }
     if (route == DGT_ROUTE_AUTO) {
-        if (g->kind == DGT_WINDOW_FIR && fir_cols && fir_synth_ok) route = DGT_ROUTE_FIR;
+        if (g->kind == DGT_WINDOW_FIR && fir_cols && fir_synth_ok && lam2 <= 8) route = DGT_ROUTE_FIR;
         else route = k.freq_shear ? DGT_ROUTE_COSET : DGT_ROUTE_SHEAR;
     }
     if (route == DGT_ROUTE_FIR && g->kind != DGT_WINDOW_FIR)
@@ -861,6 +889,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
 
     if (route == DGT_ROUTE_FIR) {
         if (!fft_ok(M, precision)) return fail(DGT_ERR_UNSUPPORTED, "FFT length M=%lld unsupported", (long long)M);
+        if (lam2 > 8) return fail(DGT_ERR_UNSUPPORTED, "FIR route supports lambda2 <= 8");
         if (!fir_cols) return fail(DGT_ERR_UNSUPPORTED, "FIR route: M=%lld too long for one tile", (long long)M);
         k.fir_cols = fir_cols;
         k.fir_group = fir_group;
@@ -1018,6 +1047,11 @@ int dgt_plan_bytes(dgt_plan_t plan, size_t* bytes) {
     if (!plan || !bytes) return fail(DGT_ERR_ARG, "null pointer");
     *bytes = plan->owned_bytes();
     return DGT_OK;
+}
+
+int dgt_plan_status(dgt_plan_t plan, void* stream) {
+    if (!plan) return fail(DGT_ERR_ARG, "null plan");
+    return plan->status_check((cudaStream_t)stream);
 }
 
 int dgt_sync(void* stream) {

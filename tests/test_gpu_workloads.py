@@ -75,6 +75,7 @@ def test_medium_pow2_full(prec, lam):
         fr = p.idgt(c, window="dual").cpu().numpy()
         for b in range(B):
             assert _rel(fr[b], _round(f[b], prec)) <= (1e-12 if prec == "f64" else 1e-5)
+        p.status()                      # no bounded device wait expired
         p.close()
     # FIR route with a Hann window of length M
     taps, center = hann_taps(M)
@@ -118,6 +119,8 @@ def test_audio_batch_full_size(prec):
     fr = pc.idgt(cc, window="dual", real=True)
     err = float(torch.linalg.vector_norm(fr - fd) / torch.linalg.vector_norm(fd))
     assert err <= (1e-12 if prec == "f64" else 1e-5)
+    ps.status()
+    pc.status()
     del cc, cs, fr
     ps.close()
     pc.close()
