@@ -111,8 +111,11 @@ template <typename C> struct FirParams {
     int64_t L, a, M, N, lam1, lam2, Lg, center;
     const C* taps;                    // Lg taps of the analysis / synthesis window
     CisTable<C> cisLM;                // exp(2 pi i e / (lam2 M))
-    const C* binph;                   // [lam2][M]: exp(-2 pi i k wn / (lam2 M)), the bin part of exp(-2 pi i l w(n)/M)
-    const C* root;                    // [lam2]: exp(-2 pi i x / lam2), the fold part (l = k + j M: x = j wn mod lam2)
+    // [lam2][Lg] modulated taps conj(h(t)) exp(-2 pi i t wn / (lam2 M)), wn = (n lam1) mod lam2.
+    // With l = ln + t (ln = time of tap 0 of column n) the modulation exp(-2 pi i l w(n)/M) of
+    // the definition splits into this tap factor and the column constant
+    // exp(-2 pi i ln wn / (lam2 M)), applied once per column after (before) the FFT.
+    const C* mtaps;
     int64_t cols;                     // time positions per CTA
     int64_t group;                    // rows transformed at once (spare buffer rows)
 };
@@ -124,6 +127,9 @@ cudaError_t launch_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>*
                                  const FirParams<cplx<T>>& fp, const FftRef& fm, int64_t B, cudaStream_t st);
 template <typename C>
 int64_t fir_seam_elems(const FirParams<C>& fp);
+// modulated taps (see FirParams::mtaps) from float64 taps h[Lg]; exact integer phase reduction
+template <typename T>
+cudaError_t launch_fir_modtaps(const double2* h, cplx<T>* out, int64_t Lg, int64_t lam2, int64_t M, cudaStream_t st);
 
 // elementwise helpers
 template <typename T>

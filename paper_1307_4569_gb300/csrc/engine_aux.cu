@@ -513,6 +513,32 @@ cudaError_t launch_fir_dual(const double2* taps, double2* out, int64_t Lg, int64
     return cudaGetLastError();
 }
 
+// Modulated FIR taps out[wn][t] = conj(h(t)) exp(-2 pi i ((t wn) mod lam2 M) / (lam2 M)),
+// computed in float64 from the exactly reduced integer phase, then rounded once to T.
+template <typename T>
+__global__ void fir_modtaps_kernel(const double2* __restrict__ h, cplx<T>* __restrict__ out, int64_t Lg, int64_t lam2,
+                                   int64_t M) {
+    const int64_t LM = lam2 * M;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < lam2 * Lg;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t wn = e / Lg, t = e - wn * Lg;
+        const int64_t r = (t % LM) * wn % LM;
+        double sn, cs;
+        sincospi(2.0 * (double)r / (double)LM, &sn, &cs);
+        const double2 v = cmulc(make_double2(cs, -sn), h[t]);
+        out[e] = mk((T)v.x, (T)v.y);
+    }
+}
+
+template <typename T>
+cudaError_t launch_fir_modtaps(const double2* h, cplx<T>* out, int64_t Lg, int64_t lam2, int64_t M, cudaStream_t st) {
+    const int64_t n = lam2 * Lg;
+    fir_modtaps_kernel<T><<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(h, out, Lg, lam2, M);
+    return cudaGetLastError();
+}
+template cudaError_t launch_fir_modtaps<float>(const double2*, float2*, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_fir_modtaps<double>(const double2*, double2*, int64_t, int64_t, int64_t, cudaStream_t);
+
 // =====================================================================================
 // Scratch of the allocation-free FIR synthesis entry point: one fixed array per GPU that
 // loads the library, held until the process exits.  Host code must not use the symbol as

@@ -62,15 +62,31 @@ __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restri
     for (int u = 0; u < B; ++u) {
         const int j = t + P::G * u;
         const int k = j % Ns;
+        if constexpr (sizeof(C) == 8) {
+            // float: one first-order twiddle w = exp(DIR 2 pi i k / (Ns R)) per butterfly, from the
+            // base table (stride 1) or the stage's compact table; w^r by a product tree of depth
+            // ceil(log2 r) <= 4, i.e. a few float roundings, instead of R - 1 strided loads
+            C wp[R];
+            wp[1] = __ldg(tw + (TS == 1 ? k : N + Ns + k));
+            if (DIR > 0) wp[1].y = -wp[1].y;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            C x = sm[spad(j + r * NR) * W + c];
-            if (r > 0) {
-                C w = __ldg(tw + r * k * TS);
-                if (DIR > 0) w.y = -w.y;
-                x = cmul(x, w);
+            for (int r = 2; r < R; ++r) wp[r] = cmul(wp[r / 2], wp[r - r / 2]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const C x = sm[spad(j + r * NR) * W + c];
+                v[u * R + r] = r > 0 ? cmul(x, wp[r]) : x;
             }
-            v[u * R + r] = x;
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                C x = sm[spad(j + r * NR) * W + c];
+                if (r > 0) {
+                    C w = __ldg(tw + r * k * TS);
+                    if (DIR > 0) w.y = -w.y;
+                    x = cmul(x, w);
+                }
+                v[u * R + r] = x;
+            }
         }
     }
     __syncthreads();
@@ -79,6 +95,10 @@ __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restri
     if constexpr (S + 1 < P::NST) p2_stages<N, DIR, W, S + 1>(c, t, sm, tw, v);
 }
 
+// Twiddle table of a length-N transform (built on the host): tw[e] = exp(-2 pi i e / N) for
+// e < N, followed, for every stage S >= 1 with N / (Ns R) > 1 (so R = 16, Ns = 16^S), by the
+// compact first-order twiddles tw[N + Ns + k] = exp(-2 pi i k / (16 Ns)), k < Ns.  The stage
+// ranges [N + Ns, N + 2 Ns) are disjoint and end below 2 N.
 // Full transform: v receives the outputs (positions from p2_out_pos).  All threads of the
 // block must call it (it synchronises the block); `sm` holds Pow2<N>::SMEM * W elements.
 template <int N, int DIR, int W, typename C, class Load>

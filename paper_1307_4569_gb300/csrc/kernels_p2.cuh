@@ -290,8 +290,8 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
 }
 
 // FIR analysis: h_n(k) gathered straight from the signal, FFT over k, store column n of c.
-// The modulation exp(-2 pi i l w(n)/M) of a sample l = k + j M is the bin phase
-// binph[wn][k] times the root of unity root[(j wn) mod lam2].
+// Sample l = ln + t (tap t of column n) enters with the modulated tap mtaps[wn][t]; the
+// column constant exp(-2 pi i ln wn / (lam2 M)) multiplies the transformed column.
 template <typename T, int N>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void* __restrict__ f, int f_real,
                                                                       cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
@@ -307,56 +307,53 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
     const int64_t b = ok ? row / fp.N : 0, n = ok ? row - b * fp.N : 0;
     int64_t ln = fp.a * n - fp.center;                        // time of tap 0, in [0, L)
     if (ln < 0) ln += fp.L;
-    const int lam2 = (int)fp.lam2;
-    const int wn = (int)((n * fp.lam1) % lam2);
-    const C* binph = fp.binph + (int64_t)wn * N;
+    const int wn = (int)((n * fp.lam1) % fp.lam2);
+    const C* mt = fp.mtaps + (int64_t)wn * fp.Lg;
     const int lnm = (int)(ln & (N - 1));
     const int Lg = (int)fp.Lg;
-    // fold j = l div M of sample l = ln + tap: j0 + (lnm + tap) div M, j0 = ln div M.  lam2 M
-    // divides L, so wrapping past L leaves j mod lam2 unchanged.  Roots for the first folds:
-    const int jm0 = (int)((ln / N) % lam2);
-    const C root0 = __ldg(fp.root + (jm0 * wn) % lam2);
-    const C root1 = __ldg(fp.root + (((jm0 + 1) % lam2) * wn) % lam2);
-    C v[16];
-    auto tap_value = [&](int k, int tap) -> C {
+    const T* fr = reinterpret_cast<const T*>(f) + b * fp.L;
+    const C* fc = reinterpret_cast<const C*>(f) + b * fp.L;
+    auto tap_value = [&](int tap) -> C {
         int64_t l = ln + tap;
         if (l >= fp.L) l -= fp.L;
-        C x;
-        if (f_real) x = mk(reinterpret_cast<const T*>(f)[b * fp.L + l], (T)0);
-        else x = reinterpret_cast<const C*>(f)[b * fp.L + l];
-        x = cmulc(x, __ldg(fp.taps + tap));
-        if (wn) {
-            const int fo = (lnm + tap) / N;                 // fold offset from tap 0
-            x = cmul(x, fo == 0 ? root0 : fo == 1 ? root1 : __ldg(fp.root + (((jm0 + fo) % lam2) * wn) % lam2));
+        const C m = __ldg(mt + tap);
+        if (f_real) {
+            const T x = fr[l];
+            return mk(x * m.x, x * m.y);
         }
-        return x;
+        return cmul(fc[l], m);
     };
+    C v[16];
     if (Lg <= N) {
         // at most one tap per bin: straight-line loads
         fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
             const int tap = (k - lnm) & (N - 1);
-            if (!ok || tap >= Lg) return mk((T)0, (T)0);
-            const C h = tap_value(k, tap);
-            return wn ? cmul(h, __ldg(binph + k)) : h;
+            return (ok && tap < Lg) ? tap_value(tap) : mk((T)0, (T)0);
         }, v);
     } else {
         fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
             C h = mk((T)0, (T)0);
             if (!ok) return h;
-            for (int tap = (k - lnm) & (N - 1); tap < Lg; tap += N) h = cadd(h, tap_value(k, tap));
-            return wn ? cmul(h, __ldg(binph + k)) : h;
+            for (int tap = (k - lnm) & (N - 1); tap < Lg; tap += N) h = cadd(h, tap_value(tap));
+            return h;
         }, v);
     }
     if (!ok) return;
     C* cr = c + row * N;
+    if (wn) {
+        const C ph = fp.cisLM(-(ln * wn));
 #pragma unroll
-    for (int i = 0; i < 16; ++i) cr[p2_out_pos<N>(t, i)] = v[i];
+        for (int i = 0; i < 16; ++i) cr[p2_out_pos<N>(t, i)] = cmul(v[i], ph);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) cr[p2_out_pos<N>(t, i)] = v[i];
+    }
 }
 
-// FIR synthesis: inverse FFT of the chunk's columns into shared rows, each multiplied by its
-// conjugate bin phase; then every sample of the chunk's segment gathers
-//   f(l) = sum_n gamma(l - a n) conj(root[(j wn) mod lam2]) row_n[l mod M],  j = l div M,
-// with the seams of the generic kernel (fir_synthesis_kernel).
+// FIR synthesis: inverse FFT of the chunk's columns into shared rows, each multiplied by the
+// conjugate column constant exp(+2 pi i ln wn / (lam2 M)); then every sample l = ln + t of
+// the chunk's segment gathers f(l) = sum_n conj(mtaps[wn][t]) row_n[l mod M], with the seams
+// of the generic kernel (fir_synthesis_kernel).
 template <int N> struct SynCfg {
     static constexpr int G = N / 16;
     static constexpr int RPB = G >= 512 ? 1 : 512 / G;                    // rows transformed at once
@@ -381,12 +378,9 @@ __global__ void __launch_bounds__(SynCfg<N>::THREADS) fir_synthesis_p2(const cpl
     const int64_t n0 = chunk * fp.cols;
     const int nc = (int)fp.cols;
     const int lam2 = (int)fp.lam2;
-    // per column: wn = (n lam1) mod lam2; per (j mod lam2, wn): conj(root[(j wn) mod lam2])
-    __shared__ int s_wn[64];
-    __shared__ C s_root[64];
-    for (int r = threadIdx.x; r < nc; r += blockDim.x) s_wn[r] = (int)(((n0 + r) * fp.lam1) % lam2);
-    for (int e = threadIdx.x; e < lam2 * lam2; e += blockDim.x)
-        s_root[e] = cconj(__ldg(fp.root + ((e / lam2) * (e % lam2)) % lam2));
+    // per column: offset wn Lg of its modulated taps, wn = (n lam1) mod lam2
+    __shared__ int s_mt[64];
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) s_mt[r] = (int)(((n0 + r) * fp.lam1) % lam2) * (int)fp.Lg;
     __syncthreads();
     for (int r0 = 0; r0 < nc; r0 += RC::RPB) {
         const int r = r0 + gi;
@@ -396,12 +390,17 @@ __global__ void __launch_bounds__(SynCfg<N>::THREADS) fir_synthesis_p2(const cpl
         C v[16];
         fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C { return ok ? cr[m] : mk((T)0, (T)0); }, v);
         if (ok) {
-            const int wn = s_wn[r];
-            const C* binph = fp.binph + (int64_t)wn * N;
+            const int64_t n = n0 + r;
+            const int wn = (int)((n * fp.lam1) % lam2);
+            if (wn) {
+                int64_t ln = fp.a * n - fp.center;
+                if (ln < 0) ln += fp.L;
+                const C ph = fp.cisLM(ln * wn);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int k = p2_out_pos<N>(t, i);
-                sm[spad(k)] = wn ? cmulc(v[i], __ldg(binph + k)) : v[i];
+                for (int i = 0; i < 16; ++i) sm[spad(p2_out_pos<N>(t, i))] = cmul(v[i], ph);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sm[spad(p2_out_pos<N>(t, i))] = v[i];
             }
         }
         __syncthreads();
@@ -417,16 +416,12 @@ __global__ void __launch_bounds__(SynCfg<N>::THREADS) fir_synthesis_p2(const cpl
         int64_t l = lstart + tt;
         if (l >= fp.L) l -= fp.L;
         const int km = (int)(l & (N - 1));
-        const C* rt = s_root + ((int)(l / N) % lam2) * lam2;
         C acc = mk((T)0, (T)0);
         const int rlo = tt - Lg + 1 <= 0 ? 0 : (tt - Lg + a) / a;
         const int rhi = min(nc - 1, tt / a);
         for (int r = rlo; r <= rhi; ++r) {
             const int tap = tt - a * r;
-            C x = cmul(rows[r * SM + spad(km)], __ldg(fp.taps + tap));
-            const int wn = s_wn[r];
-            if (wn) x = cmul(x, rt[wn]);
-            acc = cadd(acc, x);
+            acc = cadd(acc, cmulc(rows[r * SM + spad(km)], __ldg(fp.mtaps + s_mt[r] + tap)));
         }
         if (tt < ov) seamL[tt] = acc;
         else if (tt >= S - ov) seamR[tt - (S - ov)] = acc;

@@ -192,6 +192,19 @@ static void cis_host(int64_t num, int64_t den, double& c, double& s) {
     s = std::sin(ang);
 }
 
+// FFT twiddles of length n: exp(-2 pi i e / n) for e < n; for a power of two n they are
+// followed by the compact per-stage tables of the power-of-two kernels (fft_p2.cuh):
+// entry n + s + k = exp(-2 pi i k / (16 s)) for s = 16^S with 16 s < n and k < s.
+static std::vector<double> twiddle_host(int64_t n) {
+    const bool p2 = n >= 16 && (n & (n - 1)) == 0;
+    std::vector<double> h(2 * (size_t)(p2 ? 2 * n : n), 0.0);
+    for (int64_t e = 0; e < n; ++e) cis_host(-e, n, h[2 * e], h[2 * e + 1]);
+    if (p2)
+        for (int64_t s = 16; 16 * s < n; s *= 16)
+            for (int64_t k = 0; k < s; ++k) cis_host(-k, 16 * s, h[2 * (n + s + k)], h[2 * (n + s + k) + 1]);
+    return h;
+}
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -302,7 +315,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     DevBuf work;                       // plan-owned workspace
     DevBuf tmpwin;                     // scratch for window set-up
     DevBuf status;                     // int flag for the Gram solve
-    DevBuf firtab;                     // FIR modulation: bin phases [lam2][M] then roots [lam2]
+    DevBuf firmt[3];                   // FIR route: modulated taps [lam2][Lg] of the windows in gam / gT
     DevBuf lossparts;
 
     const FftRef* fft(int64_t n) {
@@ -317,9 +330,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         if (n + 1 > tile_cap<T>())
             return fail(DGT_ERR_UNSUPPORTED, "FFT length %lld exceeds the shared-memory tile (%lld)", (long long)n,
                         (long long)tile_cap<T>());
-        std::vector<double> h(2 * n);
-        for (int64_t e = 0; e < n; ++e) cis_host(-e, n, h[2 * e], h[2 * e + 1]);
-        DGT_TRY(upload_cplx<T>(t->buf, h, st));
+        DGT_TRY(upload_cplx<T>(t->buf, twiddle_host(n), st));
         t->ref.tw = t->buf.p;
         tw[n] = std::move(t);
         return DGT_OK;
@@ -358,7 +369,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     size_t ws_bytes(int64_t B) const override { return layout(B).total; }
     size_t owned_bytes() const override {
         size_t s = sigma.bytes + g64.bytes + gT.bytes + work.bytes + tmpwin.bytes + status.bytes + lossparts.bytes;
-        for (int i = 0; i < 3; ++i) s += zg[i].bytes + gam[i].bytes;
+        for (int i = 0; i < 3; ++i) s += zg[i].bytes + gam[i].bytes + firmt[i].bytes;
         for (auto& kv : tw) s += kv.second->buf.bytes;
         s += cisL.hi.bytes + cisL.lo.bytes + cis2L.hi.bytes + cis2L.lo.bytes + cis2N.hi.bytes + cis2N.lo.bytes +
              cisLM.hi.bytes + cisLM.lo.bytes;
@@ -435,15 +446,6 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         // FFT tables
         if (k.route == DGT_ROUTE_FIR) {
             DGT_TRY(add_fft(k.M, st));
-            // exp(-2 pi i l wn / (lam2 M)) with l = k + j M splits into the bin phase
-            // exp(-2 pi i k wn / (lam2 M)) and the root exp(-2 pi i (j wn mod lam2) / lam2)
-            std::vector<double> h(2 * (k.lam2 * k.M + k.lam2));
-            for (int64_t wn = 0; wn < k.lam2; ++wn)
-                for (int64_t kk = 0; kk < k.M; ++kk)
-                    cis_host(-(kk * wn), k.lam2 * k.M, h[2 * (wn * k.M + kk)], h[2 * (wn * k.M + kk) + 1]);
-            for (int64_t x = 0; x < k.lam2; ++x)
-                cis_host(-x, k.lam2, h[2 * (k.lam2 * k.M + x)], h[2 * (k.lam2 * k.M + x) + 1]);
-            DGT_TRY(upload_cplx<T>(firtab, h, st));
         } else {
             DGT_TRY(add_fft(k.sep.d, st));
             DGT_TRY(add_fft(k.sep.M, st));
@@ -475,7 +477,10 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     int build_factor(int slot, const C* gw, cudaStream_t st) {
         const PlanCore& k = core;
         if (k.route == DGT_ROUTE_FIR) {
-            zg_ok[slot] = true;      // FIR route uses the taps directly
+            // FIR route: the taps themselves plus their modulated copies (slot 0 is built from
+            // the float64 window g64, which holds the same taps)
+            DGT_TRY(build_fir_mt(slot, (const double2*)g64.p, st));
+            zg_ok[slot] = true;
             return DGT_OK;
         }
         DGT_TRY(zg[slot].alloc(sizeof(C) * (size_t)k.J * k.L));
@@ -500,6 +505,13 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         return DGT_OK;
     }
 
+    int build_fir_mt(int slot, const double2* taps64, cudaStream_t st) {
+        const PlanCore& k = core;
+        DGT_TRY(firmt[slot].alloc(sizeof(C) * (size_t)k.lam2 * k.Lg));
+        CUDA_TRY(launch_fir_modtaps<T>(taps64, (C*)firmt[slot].p, k.Lg, k.lam2, k.M, st));
+        return DGT_OK;
+    }
+
     int set_window(const void* g, int is_real, cudaStream_t st) override {
         const PlanCore& k = core;
         const int64_t n = k.win_kind == DGT_WINDOW_FIR ? k.Lg : k.L;
@@ -520,7 +532,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             ws = (char*)work.p;
         }
         if (k.route == DGT_ROUTE_FIR) {
-            FirParams<C> fp = fir_params((const C*)gT.p);
+            FirParams<C> fp = fir_params(0);
             KTRY("fir_analysis", st, launch_fir_analysis<T>(f, f_real, (C*)c, fp, *fft(k.M), B, st));
             return DGT_OK;
         }
@@ -543,13 +555,14 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         return DGT_OK;
     }
 
-    FirParams<C> fir_params(const C* taps) const {
+    // FIR parameters for window slot 0 (analysis / adjoint), 1 (dual) or 2 (tight)
+    FirParams<C> fir_params(int which) const {
         const PlanCore& k = core;
         FirParams<C> fp{};
         fp.L = k.L; fp.a = k.a; fp.M = k.M; fp.N = k.N; fp.lam1 = k.lam1; fp.lam2 = k.lam2;
-        fp.Lg = k.Lg; fp.center = k.center; fp.taps = taps; fp.cisLM = cisLM.tab; fp.cols = k.fir_cols;
-        fp.binph = (const C*)firtab.p;
-        fp.root = fp.binph ? fp.binph + k.lam2 * k.M : nullptr;
+        fp.Lg = k.Lg; fp.center = k.center; fp.cisLM = cisLM.tab; fp.cols = k.fir_cols;
+        fp.taps = which == 0 ? (const C*)gT.p : (const C*)gam[which].p;
+        fp.mtaps = (const C*)firmt[which].p;
         fp.group = k.fir_group;
         return fp;
     }
@@ -573,6 +586,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             if (k.route == DGT_ROUTE_FIR) {
                 DGT_TRY(gam[which].alloc(sizeof(C) * k.Lg));
                 CUDA_TRY(launch_convert<double, T>(g64o.p, 0, (C*)gam[which].p, k.Lg, st));
+                DGT_TRY(build_fir_mt(which, (const double2*)g64o.p, st));
                 zg_ok[which] = true;
                 CUDA_TRY(cudaStreamSynchronize(st));
                 return DGT_OK;
@@ -601,9 +615,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         if (!radix_plan(cg.d, twd.ref.pl) || cg.d + 1 > tile_cap<double>())
             return fail(DGT_ERR_UNSUPPORTED, "dual window: Zak length %lld unsupported", (long long)cg.d);
         {
-            std::vector<double> h(2 * cg.d);
-            for (int64_t e = 0; e < cg.d; ++e) cis_host(-e, cg.d, h[2 * e], h[2 * e + 1]);
-            DGT_TRY(upload_cplx<double>(twd.buf, h, st));
+            DGT_TRY(upload_cplx<double>(twd.buf, twiddle_host(cg.d), st));
             twd.ref.tw = twd.buf.p;
         }
         CisBuf<double> cisL64;
@@ -655,8 +667,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             if (!k.fir_synth_ok)
                 return fail(DGT_ERR_UNSUPPORTED, "FIR synthesis: %lld columns per tile cannot cover a window of %lld",
                             (long long)k.fir_cols, (long long)k.Lg);
-            const C* taps = which == 0 ? (const C*)gT.p : (const C*)gam[which].p;
-            FirParams<C> fp = fir_params(taps);
+            FirParams<C> fp = fir_params(which);
             KTRY("fir_synthesis", st, launch_fir_synthesis<T>((const C*)c, f, f_real, (C*)(ws + ly.seams), fp, *fft(k.M), B, st));
             return DGT_OK;
         }
@@ -757,8 +768,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         if (!zg_ok[which])
             return fail(DGT_ERR_ARG, "the dual / tight window is not cached yet (call dgt_window_dual/_tight first)");
         if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
-        const C* taps = which == 0 ? (const C*)gT.p : (const C*)gam[which].p;
-        FirParams<C> fp = fir_params(taps);
+        FirParams<C> fp = fir_params(which);
         const size_t need = sizeof(C) * (size_t)B * fir_seam_elems(fp);
         if (need > kNoAllocScratchBytes)
             return fail(DGT_ERR_UNSUPPORTED, "allocation-free synthesis needs %zu bytes of scratch; the fixed array holds %zu",
@@ -1127,9 +1137,7 @@ int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, vo
         TwTable<float> t;
         if (!radix_plan(n, t.ref.pl) || n + 1 > tile_cap<float>())
             return fail(DGT_ERR_UNSUPPORTED, "length %lld", (long long)n);
-        std::vector<double> h(2 * n);
-        for (int64_t e = 0; e < n; ++e) cis_host(-e, n, h[2 * e], h[2 * e + 1]);
-        DGT_TRY(upload_cplx<float>(t.buf, h, st));
+        DGT_TRY(upload_cplx<float>(t.buf, twiddle_host(n), st));
         t.ref.tw = t.buf.p;
         CUDA_TRY(launch_fft_rows_test<float>((const float2*)in, (float2*)out, t.ref, direction, howmany, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -1137,9 +1145,7 @@ int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, vo
         TwTable<double> t;
         if (!radix_plan(n, t.ref.pl) || n + 1 > tile_cap<double>())
             return fail(DGT_ERR_UNSUPPORTED, "length %lld", (long long)n);
-        std::vector<double> h(2 * n);
-        for (int64_t e = 0; e < n; ++e) cis_host(-e, n, h[2 * e], h[2 * e + 1]);
-        DGT_TRY(upload_cplx<double>(t.buf, h, st));
+        DGT_TRY(upload_cplx<double>(t.buf, twiddle_host(n), st));
         t.ref.tw = t.buf.p;
         CUDA_TRY(launch_fft_rows_test<double>((const double2*)in, (double2*)out, t.ref, direction, howmany, st));
         CUDA_TRY(cudaStreamSynchronize(st));
