@@ -100,6 +100,25 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------------------------------
+# replicas: one process per GPU, each on its own signals; no data-path collective
+# -------------------------------------------------------------------------------------
+def replica_start(rank: int, batch: int) -> int:
+    """Index of the first signal of rank `rank` (signals [start, start + batch) of the stream)."""
+    return rank * batch
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """Max of a per-rank float over the process group (timing: the slowest replica)."""
+    if world <= 1:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------------------------------
 # the step
 # -------------------------------------------------------------------------------------
 def make_plans(w, prec, torch):
@@ -138,6 +157,42 @@ def algorithmic_bytes(name, w, B, csz, rsz, J):
     return table.get(name)
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_audio_batch_f32.json")
+
+
+def kernel_sources_sha256() -> str:
+    """Hash of the CUDA sources and the C header, in the order the traffic file was hashed."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1307_4569_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
+                   + glob.glob(os.path.join(csrc, "*.h"))) + [os.path.join(ROOT, "include", "dgt.h")]
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, B):
+    """ncu DRAM bytes per launch of `kernel` for B signals, from the committed capture; None when
+    the kernels changed since the capture (source hash differs) or the kernel was not captured."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None, "no capture"
+    if d.get("sources_sha256") != kernel_sources_sha256():
+        return None, "capture predates the current kernel sources"
+    v = d.get("bytes_per_launch", {}).get(kernel)
+    if v is None:
+        return None, "kernel not captured"
+    return v * B / (d["batch_captured"] * d["scale"]), "ncu capture at %d signals scaled to %d" % (
+        d["batch_captured"], B)
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -153,7 +208,8 @@ def run_ours(args, rank, world):
 
     bld.build()
 
-    f_host = torch.from_numpy(signal_batch(w, count=B, cfg_id=1).astype(np.float32)).pin_memory()
+    f_host = torch.from_numpy(signal_batch(w, count=B, cfg_id=1, start=replica_start(rank, B))
+                              .astype(np.float32)).pin_memory()
     f = f_host.to(dev)
     coefs_per_step = 6 * B * w.M * w.N
 
@@ -185,11 +241,7 @@ def run_ours(args, rank, world):
             buf = __import__("ctypes").create_string_buffer(1 << 16)
             K.check(K.lib().dgt_profile_stop(buf, len(buf)))
             prof = json.loads(buf.value.decode())
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
         return ms, prof, t0, t1
 
     clocks = ClockSampler(dev.index if dev.index is not None else 0)
@@ -230,11 +282,7 @@ def run_ours(args, rank, world):
         e2e_step()
     a1.record()
     torch.cuda.synchronize()
-    e2e_ms = a0.elapsed_time(a1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(a0.elapsed_time(a1) / e2e_steps, world, dev)
     te = time.time()
     clocks.stop()
     clk = clocks.summary(t0, te)
@@ -271,20 +319,19 @@ def run_ours(args, rank, world):
     if dom:
         ab = algorithmic_bytes(dom, w, B, 8, 4, 2)
         ach = ab / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e9
-        traffic = None
-        tf = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tf):
-            try:
-                traffic = json.load(open(tf)).get(dom)
-            except Exception:
-                traffic = None
+        traffic, tnote = measured_traffic(dom, B)
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_kind": peak_kind, "traffic": traffic,
+                "frac": ach / peak, "peak_kind": peak_kind, "traffic": traffic, "traffic_note": tnote,
                 "algorithmic_bytes_per_launch": ab}
     launches = sum(v["launches"] for v in (prof or {}).values())
     step_bytes = 3 * 2 * B * (w.L * 4 + w.M * w.N * 8)
     path = {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
             "frac_of_peak": step_bytes / (ms * 1e-3) / 1e9 / peak, "frac_of_8tbs": step_bytes / (ms * 1e-3) / 8e12}
+
+    # ---------------- serving loop (mixed request stream) ----------------
+    serve = None
+    if args.serve_seconds > 0 and rank == 0:      # replicas: the serving run is a one-GPU measurement
+        serve = run_serve(args.serve_seconds)
 
     # ---------------- CPU baseline (oracle), rank 0 only ----------------
     cpu = None
@@ -309,9 +356,46 @@ def run_ours(args, rank, world):
         "fp64": fp64,
         "clocks": clk,
         "reconstruction_rel_err": err,
+        "serve": serve,
         "cpu_baseline": cpu,
     }
     return line
+
+
+def run_serve(seconds, rate=2000.0, cap_bytes=40 << 30, seed=4, infeasible_every=500, max_batch=64):
+    """The serving workload: Poisson request stream over the four power-of-two lengths (mixed
+    lattices, windows and operations, float32) through the continuous-batching scheduler on
+    the library.  Plans are built and exercised before the clock starts.  Latency of a request =
+    time its result is in pinned host memory - its scheduled arrival time."""
+    import torch
+
+    from paper_1307_4569_gb300.serve import GpuExecutor, Scheduler, request_key
+    from workloads import serve_requests
+
+    reqs = serve_requests(rate, seconds, seed=seed, infeasible_every=infeasible_every)
+    ex = GpuExecutor("f32")
+    keys = sorted({request_key(r) for r in reqs if r.feasible})
+    t0 = time.time()
+    ex.warm(keys)
+    warm_s = time.time() - t0
+    st = Scheduler(ex, cap_bytes, max_batch=max_batch, max_inflight=len(ex.streams)).run(reqs)
+    out = st.summary()
+    import numpy as np
+
+    by_len = {}
+    for L in sorted({r.L for r in reqs}):
+        lat = [s.latency for s, r in zip(st.served, reqs) if r.L == L and s.status == "ok"]
+        if lat:
+            by_len[str(L)] = {"n": len(lat), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                              "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+    out["by_length"] = by_len
+    out.update({"rate_per_s": rate, "seconds": seconds, "cap_bytes": cap_bytes, "plans": len(keys),
+                "plan_warmup_s": warm_s, "redraws": int(sum(r.redraws for r in reqs)),
+                "latency": "result in pinned host memory - scheduled arrival (open loop)",
+                "precision": "f32"})
+    ex.close()
+    torch.cuda.synchronize()
+    return out
 
 
 def make_plan_names():
@@ -406,6 +490,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-procs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0, help="signals per step (default: the workload's 64)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="length of the serving run (Poisson 2000 requests/s); 0 skips it")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -1,4 +1,4 @@
-// Power-of-two FFT with compile-time length N (16 <= N <= 8192), 16 values per thread.
+// Power-of-two FFT with compile-time length N (16 <= N <= 16384), 16 values per thread.
 //
 // A transform is computed by G = N/16 threads (index t).  Stage s has radix R_s = 16, except
 // the last stage whose radix is 2^(log2 N mod 4) when that is not 0; each thread performs
@@ -21,7 +21,7 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 __device__ __forceinline__ int spad(int e) { return e + (e >> 4); }
 
 template <int N> struct Pow2 {
-    static_assert(N >= 16 && N <= 8192 && (N & (N - 1)) == 0, "power of two in [16, 8192]");
+    static_assert(N >= 16 && N <= 16384 && (N & (N - 1)) == 0, "power of two in [16, 16384]");
     static constexpr int LOG = ilog2c(N);
     static constexpr int G = N / 16;
     static constexpr int NST = (LOG + 3) / 4;

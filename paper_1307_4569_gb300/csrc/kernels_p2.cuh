@@ -444,6 +444,16 @@ __global__ void __launch_bounds__(SynCfg<N>::THREADS) fir_synthesis_p2(const cpl
         default: return cudaErrorNotSupported;  \
     }
 
+// Row transforms (one length-M FFT per coefficient column) also come in N = 16384 for float:
+// 1024 threads, 139 KB of shared memory per transform.  Float64 rows of that length do not
+// fit one CTA's shared memory.
+#define P2_SWITCH_ROWS(NV, CALL)                                                         \
+    if ((NV) == 16384) {                                                                 \
+        if constexpr (sizeof(T) == 4) { constexpr int NN = 16384; CALL; }                \
+        else return cudaErrorNotSupported;                                               \
+    }                                                                                    \
+    P2_SWITCH(NV, CALL)
+
 inline bool p2_len_ok(int64_t n) { return n >= 128 && n <= 8192 && (n & (n - 1)) == 0; }
 
 template <typename T, int N>
@@ -577,12 +587,12 @@ cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, 
 template <typename T>
 cudaError_t p2_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const void* tw,
                         const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
-    P2_SWITCH(g.M, return (p2_fft_post_n<T, NN>(y, c, g, J, tw, pp, B, st)))
+    P2_SWITCH_ROWS(g.M, return (p2_fft_post_n<T, NN>(y, c, g, J, tw, pp, B, st)))
 }
 template <typename T>
 cudaError_t p2_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const void* tw,
                         const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
-    P2_SWITCH(g.M, return (p2_pre_ifft_n<T, NN>(c, y, g, J, tw, pp, B, st)))
+    P2_SWITCH_ROWS(g.M, return (p2_pre_ifft_n<T, NN>(c, y, g, J, tw, pp, B, st)))
 }
 template <typename T>
 cudaError_t p2_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp, const void* tw,

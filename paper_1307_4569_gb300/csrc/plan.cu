@@ -205,6 +205,9 @@ static std::vector<double> twiddle_host(int64_t n) {
     return h;
 }
 
+// the 16384-point float row transform of the power-of-two kernels (beyond the generic tile)
+static bool row_only_len_ok(int64_t n, int precision) { return precision == DGT_F32 && n == 16384; }
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -322,12 +325,14 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         auto it = tw.find(n);
         return it == tw.end() ? nullptr : &it->second->ref;
     }
-    int add_fft(int64_t n, cudaStream_t st) {
+    // rows: the length is only used by the row kernels (fft_post / pre_ifft), which also have
+    // a 16384-point float path beyond the generic shared-memory tile
+    int add_fft(int64_t n, cudaStream_t st, bool rows = false) {
         if (tw.count(n)) return DGT_OK;
         auto t = std::make_unique<TwTable<T>>();
         if (!radix_plan(n, t->ref.pl))
             return fail(DGT_ERR_UNSUPPORTED, "FFT length %lld has a prime factor above 7", (long long)n);
-        if (n + 1 > tile_cap<T>())
+        if (n + 1 > tile_cap<T>() && !(rows && row_only_len_ok(n, sizeof(T) == 4 ? DGT_F32 : DGT_F64)))
             return fail(DGT_ERR_UNSUPPORTED, "FFT length %lld exceeds the shared-memory tile (%lld)", (long long)n,
                         (long long)tile_cap<T>());
         DGT_TRY(upload_cplx<T>(t->buf, twiddle_host(n), st));
@@ -448,7 +453,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             DGT_TRY(add_fft(k.M, st));
         } else {
             DGT_TRY(add_fft(k.sep.d, st));
-            DGT_TRY(add_fft(k.sep.M, st));
+            DGT_TRY(add_fft(k.sep.M, st, true));
             if (k.freq_shear) {
                 DGT_TRY(add_fft(k.L1, st));
                 DGT_TRY(add_fft(k.L2, st));
@@ -722,7 +727,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         // through the coset decomposition (any route gives the same coefficients)
         const SepGeom& cg = k.coset_sep;
         DGT_TRY(add_fft(cg.d, st));
-        DGT_TRY(add_fft(cg.M, st));
+        DGT_TRY(add_fft(cg.M, st, true));
         const FftRef* fd = fft(cg.d);
         PostParams<C> pp{};
         pp.mode = POST_COSET;
@@ -814,6 +819,8 @@ static bool fft_ok(int64_t n, int precision) {
     if (!radix_plan(n, pl)) return false;
     return precision == DGT_F64 ? n + 1 <= tile_cap<double>() : n + 1 <= tile_cap<float>();
 }
+// lengths usable as the row length M of the Zak routes (fft_post / pre_ifft)
+static bool fft_rows_ok(int64_t n, int precision) { return fft_ok(n, precision) || row_only_len_ok(n, precision); }
 
 static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t lam1, int64_t lam2, const dgt_window* g,
                        int route, int precision, cudaStream_t st) {
@@ -934,7 +941,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
         k.L2 = L / b1;
     }
     if (route != DGT_ROUTE_FIR) {
-        if (!fft_ok(k.sep.d, precision) || !fft_ok(k.sep.M, precision))
+        if (!fft_ok(k.sep.d, precision) || !fft_rows_ok(k.sep.M, precision))
             return fail(DGT_ERR_UNSUPPORTED, "separable FFT lengths d=%lld, M=%lld unsupported", (long long)k.sep.d,
                         (long long)k.sep.M);
     }

@@ -192,3 +192,29 @@ def test_differentiable_full_size_gradients():
     assert abs(loss.item() - lv) <= 1e-10 * abs(lv)
     assert _rel(ft.grad.cpu().numpy()[0], gf) <= 1e-10
     assert _rel(gt.grad.cpu().numpy(), gg) <= 1e-10
+
+
+# -------------------------------------------------------------------------------------
+# M = 16384 (the largest serving lattice, L = 2^20, a = 2048): the 16384-point float row path
+# -------------------------------------------------------------------------------------
+@pytest.mark.parametrize("lam", [(1, 2), (0, 1)])
+def test_rows_16384_f32(lam):
+    L, a, M = 1 << 18, 1024, 16384
+    l1, l2 = lam
+    prec = "f32"
+    g = gaussian_window(L)
+    f = complex_normal(L, 21, l2)[None, :]
+    ref = OD.dgt_coset(_round(f[0], prec), _round(g, prec), a, M, l1, l2).T
+    for route in ("coset", "shear"):
+        p = _plan(L, a, M, l1, l2, _round(g, prec), route=route, precision=prec)
+        c = p.dgt(_dev(_round(f, prec), prec))
+        assert _rel(c.cpu().numpy()[0], ref) <= TOL[prec], (route, p.info)
+        fr = p.idgt(c, window="dual").cpu().numpy()
+        assert _rel(fr[0], _round(f[0], prec)) <= 1e-5
+        p.status()
+        p.close()
+    # float64 rows of this length do not fit one CTA: the coset route (rows of length M) says so
+    from paper_1307_4569_gb300 import DGTError
+
+    with pytest.raises(DGTError, match="DGT_ERR_UNSUPPORTED"):
+        _plan(L, a, M, l1, l2, g, route="coset", precision="f64")
