@@ -66,6 +66,18 @@ struct ModU64 {
     }
     // (x * y) mod d for 0 <= x, y < d
     __host__ __device__ __forceinline__ uint64_t mulmod(uint64_t x, uint64_t y) const { return mod(x * y); }
+    // floor(x / d), same estimate and corrections
+    __host__ __device__ __forceinline__ uint64_t div(uint64_t x) const {
+#ifdef __CUDA_ARCH__
+        uint64_t q = __umul64hi(x, m);
+#else
+        uint64_t q = (uint64_t)(((unsigned __int128)x * m) >> 64);
+#endif
+        uint64_t r = x - q * d;
+        if (r >= d) { ++q; r -= d; }
+        if (r >= d) ++q;
+        return q;
+    }
 };
 
 inline ModU64 make_mod(uint64_t d) {

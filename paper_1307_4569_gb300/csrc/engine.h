@@ -44,6 +44,8 @@ template <typename C> struct PostParams {
     CisTable<C> cisL;                 // exp(2 pi i e / L)
     CisTable<C> cis2N;                // exp(2 pi i e / (2N)) = exp(pi i e / N)
     ModU64 mL, mN, m2N;               // reductions modulo L, N, 2N
+    ModU64 mb;                        // division by b
+    ModU64 mJN, mNs;                  // row = (b J + j) Ns + n of Y: division by J Ns and Ns (set by the launchers)
 };
 
 // Signal pre-processing inside the factorisation / FFT_L passes.
@@ -116,6 +118,7 @@ template <typename C> struct FirParams {
     // the definition splits into this tap factor and the column constant
     // exp(-2 pi i ln wn / (lam2 M)), applied once per column after (before) the FFT.
     const C* mtaps;
+    ModU64 mN;                        // division by N (row = b N + n)
     int64_t cols;                     // time positions per CTA
     int64_t group;                    // rows transformed at once (spare buffer rows)
 };

@@ -48,7 +48,7 @@ __device__ __forceinline__ int64_t out_index(const PostParams<C>& pp, const SepG
         case POST_SHEAR0: {
             const uint64_t L = pp.L;
             const uint64_t sa = pp.mL.mulmod((uint64_t)pp.s1a_modL, (uint64_t)n);
-            const int64_t rot = (int64_t)((sa ? L - sa : 0) / (uint64_t)pp.b);
+            const int64_t rot = (int64_t)pp.mb.div(sa ? L - sa : 0);
             const uint64_t nn = pp.m2N.mulmod((uint64_t)n, (uint64_t)n);
             ph = pp.cis2N.at(pp.m2N.mulmod((uint64_t)pp.C1_2N, nn));
             int64_t mo = m + rot;
@@ -67,8 +67,8 @@ __device__ __forceinline__ int64_t out_index(const PostParams<C>& pp, const SepG
             const uint64_t inner = pp.m2N.mod(pp.m2N.mulmod((uint64_t)pp.C4_2N, mr2) + pp.m2N.mulmod((uint64_t)pp.C5_2N, k2));
             const uint64_t t2 = pp.m2N.mulmod(mr2, inner);
             ph = pp.cis2N.at(t1 >= t2 ? t1 - t2 : t1 + twoN - t2);
-            const uint64_t kt = pp.mL.mod(pp.mL.mulmod((uint64_t)pp.s1ar_L, pp.mL.mod(k)) +
-                                          pp.mL.mulmod((uint64_t)pp.C6_L, pp.mL.mod(mr))) / (uint64_t)pp.b;
+            const uint64_t kt = pp.mb.div(pp.mL.mod(pp.mL.mulmod((uint64_t)pp.s1ar_L, pp.mL.mod(k)) +
+                                                    pp.mL.mulmod((uint64_t)pp.C6_L, pp.mL.mod(mr))));
             return (b * pp.N + (int64_t)mt) * pp.M + (int64_t)kt;
         }
         default:

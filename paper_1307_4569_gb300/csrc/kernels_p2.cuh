@@ -31,6 +31,7 @@ template <int N> struct RowCfg {
     static constexpr int G = N / 16;
     static constexpr int RPB = G >= 256 ? 1 : 256 / G;                   // rows per CTA
     static constexpr int THREADS = RPB * G;
+    static constexpr int MINB = 65536 / (THREADS * 64) > 0 ? 65536 / (THREADS * 64) : 1;   // <= 64 registers
 };
 
 template <typename K> static cudaError_t p2_smem(K kernel, size_t bytes) {
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MINB) pro
     C* sm = reinterpret_cast<C*>(smem_raw);
     const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
     const int64_t b = blockIdx.z;
-    const int64_t j = blockIdx.y / g.q, w = blockIdx.y % g.q;
+    const int64_t j = (int)blockIdx.y / (int)g.q, w = (int)blockIdx.y % (int)g.q;
     const int64_t k = (int64_t)blockIdx.x * CF::W + c;
     const bool ok = k < g.M;
     int64_t colG = k - g.a * w;
@@ -212,8 +213,11 @@ __device__ __forceinline__ RowMap<C> row_map(const PostParams<C>& pp, const SepG
     return r;
 }
 
-// fft_post: FFT over k of rows of Y, route post-processing, store into c
-template <typename T, int N>
+// fft_post: FFT over k of rows of Y, route post-processing, store into c.  SH1 selects the
+// per-coefficient index map of the frequency-shear branch; the other modes need one
+// (base, rotation, phase) per row, computed before the transform so that it is not live
+// beside the 16 values.  Separate instantiations keep the register budget of each.
+template <typename T, int N, bool SH1>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>* __restrict__ y,
                                                                   cplx<T>* __restrict__ c, SepGeom g, int64_t J,
                                                                   int64_t rows_total, const cplx<T>* __restrict__ tw,
@@ -226,14 +230,13 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>*
     const int64_t row = (int64_t)blockIdx.x * RC::RPB + gi;
     const bool ok = row < rows_total;
     const C* yr = y + row * N;
-    C v[16];
-    fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
-    if (!ok) return;
-    const int64_t Nsep = g.d * g.q;
-    const int64_t b = row / (J * Nsep);
-    const int64_t rem = row - b * J * Nsep;
-    const int64_t j = rem / Nsep, nn = rem - j * Nsep;
-    if (pp.mode == POST_SHEAR1) {
+    const int64_t b = ok ? (int64_t)pp.mJN.div((uint64_t)row) : 0;
+    const int64_t rem = row - b * (int64_t)pp.mJN.d;
+    const int64_t j = ok ? (int64_t)pp.mNs.div((uint64_t)rem) : 0, nn = ok ? rem - j * (int64_t)pp.mNs.d : 0;
+    if constexpr (SH1) {
+        C v[16];
+        fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
+        if (!ok) return;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             C ph;
@@ -241,7 +244,11 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>*
             c[o] = cmul(v[i], ph);
         }
     } else {
-        const RowMap<C> rm = row_map(pp, g, b, j, nn);
+        RowMap<C> rm{};
+        if (ok) rm = row_map(pp, g, b, j, nn);
+        C v[16];
+        fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
+        if (!ok) return;
         C* cb = c + rm.base;
         const int rot = (int)rm.rot;
 #pragma unroll
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>*
 }
 
 // pre_ifft: gather c with conjugate phases, unnormalised inverse FFT, store rows of Y
-template <typename T, int N>
+template <typename T, int N, bool SH1>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>* __restrict__ c,
                                                                   cplx<T>* __restrict__ y, SepGeom g, int64_t J,
                                                                   int64_t rows_total, const cplx<T>* __restrict__ tw,
@@ -262,12 +269,11 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
     C* sm = reinterpret_cast<C*>(smem_raw) + gi * Pow2<N>::SMEM;
     const int64_t row = (int64_t)blockIdx.x * RC::RPB + gi;
     const bool ok = row < rows_total;
-    const int64_t Nsep = g.d * g.q;
-    const int64_t b = ok ? row / (J * Nsep) : 0;
-    const int64_t rem = row - b * J * Nsep;
-    const int64_t j = ok ? rem / Nsep : 0, nn = ok ? rem - j * Nsep : 0;
+    const int64_t b = ok ? (int64_t)pp.mJN.div((uint64_t)row) : 0;
+    const int64_t rem = row - b * (int64_t)pp.mJN.d;
+    const int64_t j = ok ? (int64_t)pp.mNs.div((uint64_t)rem) : 0, nn = ok ? rem - j * (int64_t)pp.mNs.d : 0;
     C v[16];
-    if (pp.mode == POST_SHEAR1) {
+    if constexpr (SH1) {
         fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
             if (!ok) return mk((T)0, (T)0);
             C ph;
@@ -292,7 +298,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
 // FIR analysis: h_n(k) gathered straight from the signal, FFT over k, store column n of c.
 // Sample l = ln + t (tap t of column n) enters with the modulated tap mtaps[wn][t]; the
 // column constant exp(-2 pi i ln wn / (lam2 M)) multiplies the transformed column.
-template <typename T, int N>
+template <typename T, int N, bool MULTI>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void* __restrict__ f, int f_real,
                                                                       cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
                                                                       int64_t rows_total,
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
     C* sm = reinterpret_cast<C*>(smem_raw) + gi * Pow2<N>::SMEM;
     const int64_t row = (int64_t)blockIdx.x * RC::RPB + gi;
     const bool ok = row < rows_total;
-    const int64_t b = ok ? row / fp.N : 0, n = ok ? row - b * fp.N : 0;
+    const int64_t b = ok ? (int64_t)fp.mN.div((uint64_t)row) : 0, n = ok ? row - b * fp.N : 0;
     int64_t ln = fp.a * n - fp.center;                        // time of tap 0, in [0, L)
     if (ln < 0) ln += fp.L;
     const int wn = (int)((n * fp.lam1) % fp.lam2);
@@ -313,6 +319,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
     const int Lg = (int)fp.Lg;
     const T* fr = reinterpret_cast<const T*>(f) + b * fp.L;
     const C* fc = reinterpret_cast<const C*>(f) + b * fp.L;
+    const C ph = wn ? fp.cisLM(-(ln * wn)) : mk((T)1, (T)0);       // column constant
     auto tap_value = [&](int tap) -> C {
         int64_t l = ln + tap;
         if (l >= fp.L) l -= fp.L;
@@ -324,8 +331,8 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
         return cmul(fc[l], m);
     };
     C v[16];
-    if (Lg <= N) {
-        // at most one tap per bin: straight-line loads
+    if constexpr (!MULTI) {
+        // Lg <= N: at most one tap per bin, straight-line loads
         fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
             const int tap = (k - lnm) & (N - 1);
             return (ok && tap < Lg) ? tap_value(tap) : mk((T)0, (T)0);
@@ -341,7 +348,6 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
     if (!ok) return;
     C* cr = c + row * N;
     if (wn) {
-        const C ph = fp.cisLM(-(ln * wn));
 #pragma unroll
         for (int i = 0; i < 16; ++i) cr[p2_out_pos<N>(t, i)] = cmul(v[i], ph);
     } else {
@@ -510,11 +516,14 @@ cudaError_t p2_fft_post_n(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_
                           const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
     using RC = RowCfg<N>;
     const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
-    auto k = fft_post_p2<T, N>;
+    auto k = pp.mode == POST_SHEAR1 ? fft_post_p2<T, N, true> : fft_post_p2<T, N, false>;
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     const int64_t rows = B * J * g.d * g.q;
-    k<<<(unsigned)((rows + RC::RPB - 1) / RC::RPB), RC::THREADS, smem, st>>>(y, c, g, J, rows, (const cplx<T>*)tw, pp);
+    PostParams<cplx<T>> q = pp;
+    q.mJN = make_mod((uint64_t)(J * g.d * g.q));
+    q.mNs = make_mod((uint64_t)(g.d * g.q));
+    k<<<(unsigned)((rows + RC::RPB - 1) / RC::RPB), RC::THREADS, smem, st>>>(y, c, g, J, rows, (const cplx<T>*)tw, q);
     return cudaGetLastError();
 }
 
@@ -523,11 +532,14 @@ cudaError_t p2_pre_ifft_n(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_
                           const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
     using RC = RowCfg<N>;
     const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
-    auto k = pre_ifft_p2<T, N>;
+    auto k = pp.mode == POST_SHEAR1 ? pre_ifft_p2<T, N, true> : pre_ifft_p2<T, N, false>;
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     const int64_t rows = B * J * g.d * g.q;
-    k<<<(unsigned)((rows + RC::RPB - 1) / RC::RPB), RC::THREADS, smem, st>>>(c, y, g, J, rows, (const cplx<T>*)tw, pp);
+    PostParams<cplx<T>> q = pp;
+    q.mJN = make_mod((uint64_t)(J * g.d * g.q));
+    q.mNs = make_mod((uint64_t)(g.d * g.q));
+    k<<<(unsigned)((rows + RC::RPB - 1) / RC::RPB), RC::THREADS, smem, st>>>(c, y, g, J, rows, (const cplx<T>*)tw, q);
     return cudaGetLastError();
 }
 
@@ -536,7 +548,7 @@ cudaError_t p2_fir_analysis_n(const void* f, int f_real, cplx<T>* c, const FirPa
                               int64_t B, cudaStream_t st) {
     using RC = RowCfg<N>;
     const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
-    auto k = fir_analysis_p2<T, N>;
+    auto k = fp.Lg > N ? fir_analysis_p2<T, N, true> : fir_analysis_p2<T, N, false>;
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     const int64_t rows = B * fp.N;

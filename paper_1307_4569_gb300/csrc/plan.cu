@@ -409,6 +409,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         pp.mL = make_mod((uint64_t)k.L);
         pp.mN = make_mod((uint64_t)k.N);
         pp.m2N = make_mod(2 * (uint64_t)k.N);
+        pp.mb = make_mod((uint64_t)k.b);
         if (k.route == DGT_ROUTE_COSET) {
             pp.mode = POST_COSET;
             pp.lam2 = k.lam2;
@@ -568,6 +569,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         fp.Lg = k.Lg; fp.center = k.center; fp.cisLM = cisLM.tab; fp.cols = k.fir_cols;
         fp.taps = which == 0 ? (const C*)gT.p : (const C*)gam[which].p;
         fp.mtaps = (const C*)firmt[which].p;
+        fp.mN = make_mod((uint64_t)k.N);
         fp.group = k.fir_group;
         return fp;
     }
@@ -737,6 +739,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         pp.mL = make_mod((uint64_t)k.L);
         pp.mN = make_mod((uint64_t)k.N);
         pp.m2N = make_mod(2 * (uint64_t)k.N);
+        pp.mb = make_mod((uint64_t)k.b);
         const size_t need = al(sizeof(C) * (size_t)B * k.L) + al(sizeof(C) * (size_t)B * k.M * k.N) +
                             2 * al(sizeof(C) * (size_t)k.lam2 * k.L);
         DevBuf scratch;
