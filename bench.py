@@ -139,6 +139,11 @@ def make_plans(w, prec, torch):
     return plans
 
 
+# full-batch passes of each hot-path kernel in one step (two Zak routes, one FIR route)
+PASSES_PER_STEP = {"zak_fwd": 2, "prod_ifft": 2, "fft_post": 2, "pre_ifft": 2, "fft_prod_adj": 2, "zak_inv": 2,
+                   "fir_analysis": 1, "fir_synthesis": 1}
+
+
 def algorithmic_bytes(name, w, B, csz, rsz, J):
     """Compulsory bytes of one launch of a hot-path kernel for B signals (inputs + outputs)."""
     L, MN = w.L, w.M * w.N
@@ -309,20 +314,29 @@ def run_ours(args, rank, world):
     kernels = {}
     total_prof_ms = sum(v["ms"] for v in prof.values()) if prof else 0.0
     for name, v in (prof or {}).items():
-        ab = algorithmic_bytes(name, w, B, 8, 4, 2)
+        passes = PASSES_PER_STEP.get(name)
+        ab_full = algorithmic_bytes(name, w, B, 8, 4, 2)
         avg = v["ms"] / v["launches"]
-        kernels[name] = {"launches": v["launches"], "ms_per_launch": avg, "share": v["ms"] / total_prof_ms,
-                         "achieved_gbs": (ab / (avg * 1e-3) / 1e9) if ab else None}
+        ent = {"launches": v["launches"], "ms_per_launch": avg, "share": v["ms"] / total_prof_ms, "achieved_gbs": None}
+        if ab_full and passes:
+            # the Zak routes run the batch in passes of a few signals: a launch covers
+            # B * passes * steps / launches signals
+            sig = B * passes * args.steps / v["launches"]
+            ab = ab_full * sig / B
+            ent.update({"signals_per_launch": sig, "algorithmic_bytes_per_launch": ab,
+                        "achieved_gbs": ab / (avg * 1e-3) / 1e9})
+        kernels[name] = ent
     ranked = sorted((k for k in kernels if kernels[k]["achieved_gbs"] is not None), key=lambda k: -kernels[k]["share"])
     dom = ranked[0] if ranked else None
     roof = None
     if dom:
-        ab = algorithmic_bytes(dom, w, B, 8, 4, 2)
-        ach = ab / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e9
-        traffic, tnote = measured_traffic(dom, B)
+        kd = kernels[dom]
+        ach = kd["achieved_gbs"]
+        traffic, tnote = measured_traffic(dom, kd["signals_per_launch"])
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": peak_kind, "traffic": traffic, "traffic_note": tnote,
-                "algorithmic_bytes_per_launch": ab}
+                "algorithmic_bytes_per_launch": kd["algorithmic_bytes_per_launch"],
+                "signals_per_launch": kd["signals_per_launch"]}
     launches = sum(v["launches"] for v in (prof or {}).values())
     step_bytes = 3 * 2 * B * (w.L * 4 + w.M * w.N * 8)
     path = {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
@@ -332,6 +346,7 @@ def run_ours(args, rank, world):
     serve = None
     if args.serve_seconds > 0 and rank == 0:      # replicas: the serving run is a one-GPU measurement
         serve = run_serve(args.serve_seconds)
+    others = run_other_configs(dev) if (args.other_configs and rank == 0) else None
 
     # ---------------- CPU baseline (oracle), rank 0 only ----------------
     cpu = None
@@ -357,9 +372,98 @@ def run_ours(args, rank, world):
         "clocks": clk,
         "reconstruction_rel_err": err,
         "serve": serve,
+        "other_configs": others,
         "cpu_baseline": cpu,
     }
     return line
+
+
+def _time_cuda(fn, steps, warmup=2):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_other_configs(dev, steps=5):
+    """The other workloads, briefly: the lambda = 1/3 batch (both routes, float32 and float64),
+    the differentiable batch (analysis + hand-written backward with the window gradient) and
+    the small float64 quincunx lattice (launch-bound latency).  Coefficients per second count
+    the coefficients produced plus consumed, as in the headline."""
+    import numpy as np
+    import torch
+
+    from paper_1307_4569_gb300 import Plan
+    from paper_1307_4569_gb300 import dgt as dgt_fn
+    from workloads import DENSE_THIRD, DIFFERENTIABLE, QUINCUNX_FP64, complex_normal, gaussian_window, \
+        noisy_gaussian_window, real_normal, signal_batch
+
+    out = {}
+    # lambda = 1/3: 128 complex signals (64 noise, 64 chirps), analysis + dual synthesis per route
+    w = DENSE_THIRD
+    f64 = signal_batch(w, cfg_id=2)
+    g = gaussian_window(w.L)
+    res = {}
+    for prec, cdt in (("f32", torch.complex64), ("f64", torch.complex128)):
+        f = torch.from_numpy(f64.astype(np.complex64 if prec == "f32" else np.complex128)).to(dev)
+        c = torch.empty((w.batch, w.N, w.M), dtype=cdt, device=dev)
+        fr = torch.empty_like(f)
+        for route in ("coset", "shear"):
+            p = Plan(w.L, w.a, w.M, w.lam1, w.lam2, g, route=route, precision=prec)
+            p.dual_window()
+
+            def step():
+                p.dgt(f, out=c)
+                p.idgt(c, window="dual", out=fr)
+
+            ms = _time_cuda(step, steps if prec == "f32" else 2)
+            err = float(torch.linalg.vector_norm(fr - f) / torch.linalg.vector_norm(f))
+            res["%s_%s" % (route, prec)] = {"ms_per_step": ms, "coef_per_s": 2 * w.batch * w.M * w.N / (ms * 1e-3),
+                                            "reconstruction_rel_err": err}
+            p.close()
+        del f, c, fr
+    out["dense_third"] = {"workload": w.name, "batch": w.batch, "step": "analysis + dual synthesis", **res}
+    torch.cuda.empty_cache()
+    # differentiable: 32 real float32 signals, learnable window, sum log(|c|^2 + 1e-6)
+    w = DIFFERENTIABLE
+    f = torch.from_numpy(np.stack([real_normal(w.L, 5, i) for i in range(w.batch)]).astype(np.float32)).to(dev)
+    gw = torch.from_numpy(noisy_gaussian_window(w.L, 5).astype(np.float32)).to(dev)
+    p = Plan(w.L, w.a, w.M, w.lam1, w.lam2, gw.cpu().numpy(), precision="f32")
+
+    def train_step():
+        ft = f.requires_grad_(True)
+        gt = gw.detach().clone().requires_grad_(True)
+        cc = dgt_fn(ft, gt, p)
+        loss = torch.log(cc.real ** 2 + cc.imag ** 2 + 1e-6).sum()
+        loss.backward()
+
+    ms = _time_cuda(train_step, steps)
+    out["differentiable"] = {"workload": w.name, "batch": w.batch, "route": p.route,
+                             "step": "analysis, loss, backward (signal and window gradients)",
+                             "ms_per_step": ms, "coef_per_s": w.batch * w.M * w.N / (ms * 1e-3)}
+    p.close()
+    del f, gw
+    torch.cuda.empty_cache()
+    # small float64 lattice: one signal, analysis + dual synthesis, both routes (latency)
+    w = QUINCUNX_FP64
+    f = torch.from_numpy(complex_normal(w.L, 1, 0)).to(dev)[None]
+    g = gaussian_window(w.L)
+    lat = {}
+    for route in ("coset", "shear"):
+        p = Plan(w.L, w.a, w.M, w.lam1, w.lam2, g, route=route, precision="f64")
+        p.dual_window()
+        lat[route + "_us"] = 1e3 * _time_cuda(lambda: p.idgt(p.dgt(f), window="dual"), 50, 5)
+        p.close()
+    out["quincunx_fp64"] = {"workload": w.name, "step": "analysis + dual synthesis of one signal", **lat}
+    return out
 
 
 def run_serve(seconds, rate=2000.0, cap_bytes=40 << 30, seed=4, infeasible_every=500, max_batch=64):
@@ -490,6 +594,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-procs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0, help="signals per step (default: the workload's 64)")
+    ap.add_argument("--other-configs", type=int, default=1, help="1: also time the other workloads briefly")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the serving run (Poisson 2000 requests/s); 0 skips it")
     args = ap.parse_args()
