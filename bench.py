@@ -141,7 +141,7 @@ def make_plans(w, prec, torch):
 
 # full-batch passes of each hot-path kernel in one step (two Zak routes, one FIR route)
 PASSES_PER_STEP = {"zak_fwd": 2, "prod_ifft": 2, "fft_post": 2, "pre_ifft": 2, "fft_prod_adj": 2, "zak_inv": 2,
-                   "fir_analysis": 1, "fir_synthesis": 1}
+                   "zak_prod_ifft": 2, "fir_analysis": 1, "fir_synthesis": 1}
 
 
 def algorithmic_bytes(name, w, B, csz, rsz, J):
@@ -156,8 +156,7 @@ def algorithmic_bytes(name, w, B, csz, rsz, J):
         "pre_ifft": B * 2 * MN * csz,
         "fft_prod_adj": B * (MN * csz + L * csz),
         "zak_inv": B * (L * csz + L * rsz),
-        "fused_analysis": B * (L * csz + MN * csz),
-        "fused_synthesis": B * (MN * csz + L * csz),
+        "zak_prod_ifft": B * (L * rsz + MN * csz),
     }
     return table.get(name)
 

@@ -177,6 +177,13 @@ cudaError_t p2_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx
 template <typename T>
 cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
                        const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
+// lengths of the power-of-two column kernels
+inline bool p2_col_len_ok(int64_t n) { return n >= 128 && n <= 8192 && (n & (n - 1)) == 0; }
+// fused Zak analysis (p = 1): zak_fwd + prod_ifft
+template <typename T>
+cudaError_t p2_zak_prod_ifft(const void* src, int src_real, int64_t sbs, const cplx<T>* zg, int64_t J, cplx<T>* y,
+                             const SepGeom& g, const void* tw, const ChirpParams<cplx<T>>& pre, int64_t B,
+                             cudaStream_t st);
 template <typename T>
 cudaError_t p2_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const void* tw,
                         const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st);

@@ -110,4 +110,20 @@ __device__ __forceinline__ void fft_p2(int c, int t, C* sm, const C* __restrict_
     if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1>(c, t, sm, tw, v);
 }
 
+// Register m of thread t holds element t + G m: the order stage 0 reads its inputs in.  The
+// outputs of fft_p2 sit at the same positions in another order (p2_out_pos); output register
+// idx holds element t + G p2_out_m(idx).  So the outputs of one transform can feed the next
+// (of the same length) without leaving the registers: v_in[p2_out_m(idx)] = v_out[idx].
+template <int N> __host__ __device__ constexpr int p2_out_m(int idx) {
+    return idx / Pow2<N>::RL + (16 / Pow2<N>::RL) * (idx % Pow2<N>::RL);
+}
+
+// Full transform of the 16 values already in registers (v[m] = element t + G m).
+template <int N, int DIR, int W, typename C>
+__device__ __forceinline__ void fft_p2_regs(int c, int t, C* sm, const C* __restrict__ tw, C (&v)[16]) {
+    using P = Pow2<N>;
+    dft16<DIR>(v);
+    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1>(c, t, sm, tw, v);
+}
+
 }  // namespace dgt

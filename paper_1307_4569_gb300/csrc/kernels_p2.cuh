@@ -159,6 +159,70 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS) fft_prod_adj_p2(const c
 }
 
 // ------------------------------------------------------------------------------------
+// Fused Zak analysis (p = 1, so K0 = L/d = M and the Zak columns are the product columns).
+// zak_prod_ifft: one CTA per tile of W columns k computes the Zak DFT of the signal columns
+// (zak_fwd), keeps ZF[.][k] in registers, and for every (j, w) forms ZF conj(ZG~_j[.][k - a w]),
+// transforms it back over xi and stores Y[b][j][w + q nu][k] / d (prod_ifft): ZF never goes
+// to memory and is read once instead of J q times.   grid (k-tiles, B)
+// (The adjoint pair fft_prod_adj + zak_inv stays two kernels: fused, the inverse Zak DFT ran
+// at the accumulating kernel's occupancy and the pair got slower.)
+// ------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_prod_ifft_p2(const void* __restrict__ src, int src_real,
+                                                                          int64_t sbs, const cplx<T>* __restrict__ zg,
+                                                                          int64_t J, cplx<T>* __restrict__ y, SepGeom g,
+                                                                          const cplx<T>* __restrict__ tw,
+                                                                          ChirpParams<cplx<T>> pre) {
+    using C = cplx<T>;
+    using CF = ColCfg<T, N>;
+    constexpr int G = Pow2<N>::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = k < g.M;
+    const int64_t K0 = g.K0;
+    C zfm[16];
+    {
+        C v[16];
+        fft_p2<N, -1, CF::W>(c, t, sm, tw, [&](int e) -> C {
+            if (!ok) return mk((T)0, (T)0);
+            const int64_t l = k + K0 * e;
+            C x = load_any<C>(src, src_real, b * sbs + l);
+            if (pre.mode == PRE_CHIRP) x = cmul(x, chirp_factor(pre, l));
+            return x;
+        }, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) zfm[p2_out_m<N>(i)] = v[i];
+    }
+    const T scale = (T)1 / (T)N;
+    const int64_t ystride = g.q * g.M;                     // Y rows w + q nu, nu = 0, 1, ...
+    for (int64_t j = 0; j < J; ++j) {
+        for (int64_t w = 0; w < g.q; ++w) {
+            int64_t colG = k - g.a * w;
+            const bool wrap = colG < 0;
+            if (wrap) colG += K0;
+            const C* zgj = zg + j * g.L + colG;
+            C v[16];
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int xi = t + G * m;
+                C x = ok ? cmulc(zfm[m], zgj[(int64_t)xi * K0]) : mk((T)0, (T)0);
+                if (wrap) x = cmulc(x, __ldg(tw + xi));
+                v[m] = x;
+            }
+            fft_p2_regs<N, +1, CF::W>(c, t, sm, tw, v);
+            if (ok) {
+                C* yb = y + ((b * J + j) * g.d * g.q + w) * g.M + k;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) yb[(int64_t)p2_out_pos<N>(t, i) * ystride] = cscale(v[i], scale);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // zak_inv: unnormalised inverse DFT over xi per column, post-op, store
 // ------------------------------------------------------------------------------------
 template <typename T, int N>
@@ -571,6 +635,19 @@ cudaError_t p2_fir_synthesis_n(const cplx<T>* c, void* f, int f_real, cplx<T>* s
     return cudaGetLastError();
 }
 
+template <typename T, int N>
+cudaError_t p2_zak_prod_ifft_n(const void* src, int src_real, int64_t sbs, const cplx<T>* zg, int64_t J, cplx<T>* y,
+                               const SepGeom& g, const void* tw, const ChirpParams<cplx<T>>& pre, int64_t B,
+                               cudaStream_t st) {
+    using CF = ColCfg<T, N>;
+    auto k = zak_prod_ifft_p2<T, N>;
+    cudaError_t e = p2_smem(k, CF::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.M + CF::W - 1) / CF::W), (unsigned)B);
+    k<<<grid, CF::THREADS, CF::SMEM, st>>>(src, src_real, sbs, zg, J, y, g, (const cplx<T>*)tw, pre);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------
 // run-time dispatch over the instantiated lengths; cudaErrorNotSupported = use the generic path
 // ------------------------------------------------------------------------------------
@@ -595,6 +672,13 @@ template <typename T>
 cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
                        const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st) {
     P2_SWITCH(d, return (p2_zak_inv_n<T, NN>(zf, zbs, dst, dst_real, dbs, K0, tw, post, scale, B, st)))
+}
+template <typename T>
+cudaError_t p2_zak_prod_ifft(const void* src, int src_real, int64_t sbs, const cplx<T>* zg, int64_t J, cplx<T>* y,
+                             const SepGeom& g, const void* tw, const ChirpParams<cplx<T>>& pre, int64_t B,
+                             cudaStream_t st) {
+    if (g.p != 1 || g.K0 != g.M) return cudaErrorNotSupported;
+    P2_SWITCH(g.d, return (p2_zak_prod_ifft_n<T, NN>(src, src_real, sbs, zg, J, y, g, tw, pre, B, st)))
 }
 template <typename T>
 cudaError_t p2_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const void* tw,

@@ -527,6 +527,13 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         return build_factor(0, (const C*)gT.p, st);
     }
 
+    // the power-of-two fused Zak kernels apply: p = 1 (so the Zak columns are the product
+    // columns, K0 = M) and a power-of-two Zak length
+    bool fused_zak() const {
+        const SepGeom& g = core.sep;
+        return g.p == 1 && g.K0 == g.M && p2_col_len_ok(g.d);
+    }
+
     // ---- analysis ---------------------------------------------------------------------
     int exec(const void* f, int f_real, void* c, int64_t B, void* wsp, cudaStream_t st) override {
         const PlanCore& k = core;
@@ -545,18 +552,26 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         C* zf = (C*)(ws + ly.zf);
         C* y = (C*)(ws + ly.y);
         const FftRef* fd = fft(k.sep.d);
-        if (k.route == DGT_ROUTE_COSET) {
-            KTRY("zak_fwd", st, launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, k.sep.d, *fd, nochirp(), B, st));
-        } else if (!k.freq_shear) {
-            KTRY("zak_fwd", st, launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 0), B, st));
-        } else {
+        // the Zak input: the signal (coset: as it is; time shear: times pchirp(s1)), or its
+        // chirped FFT_L (frequency shear)
+        const void* zsrc = f;
+        int zreal = f_real;
+        ChirpParams<C> pre = k.route == DGT_ROUTE_COSET ? nochirp() : chirp(k.sh.s1, 0);
+        if (k.freq_shear) {
             C* tmp = (C*)(ws + ly.tmp);
             C* fh = (C*)(ws + ly.fh);
             KTRY("fftL_cols", st, launch_fftL_cols<T>(f, f_real, tmp, k.L1, k.L2, -1, *fft(k.L1), chirp(k.sh.s1, 0), cisL.tab, B, st));
             KTRY("fftL_rows", st, launch_fftL_rows<T>(tmp, fh, 0, k.L1, k.L2, -1, *fft(k.L2), chirp(-k.sh.s0, 0), (T)1, B, st));
-            KTRY("zak_fwd", st, launch_zak_fwd<T>(fh, 0, k.L, zf, k.L, k.L, k.sep.d, *fd, nochirp(), B, st));
+            zsrc = fh;
+            zreal = 0;
+            pre = nochirp();
         }
-        KTRY("prod_ifft", st, launch_prod_ifft<T>(zf, (const C*)zg[0].p, k.J, y, k.sep, *fd, B, st));
+        if (fused_zak()) {
+            KTRY("zak_prod_ifft", st, p2_zak_prod_ifft<T>(zsrc, zreal, k.L, (const C*)zg[0].p, k.J, y, k.sep, fd->tw, pre, B, st));
+        } else {
+            KTRY("zak_fwd", st, launch_zak_fwd<T>(zsrc, zreal, k.L, zf, k.L, k.L, k.sep.d, *fd, pre, B, st));
+            KTRY("prod_ifft", st, launch_prod_ifft<T>(zf, (const C*)zg[0].p, k.J, y, k.sep, *fd, B, st));
+        }
         KTRY("fft_post", st, launch_fft_post<T>(y, (C*)c, k.sep, k.J, *fft(k.sep.M), post(), B, st));
         return DGT_OK;
     }
