@@ -39,18 +39,34 @@ template <int N> __device__ __forceinline__ int p2_out_pos(int t, int idx) {
     return t + P::G * u + r * P::NSL;
 }
 
-template <int N, int DIR, int W, int S, typename C>
+// FA: exchange addresses as one base per butterfly plus compile-time offsets (fewer integer
+// instructions); !FA recomputes each padded index (fewer live registers, which the kernels
+// that hold a second set of 16 values need to stay within 128)
+template <int N, int DIR, int W, int S, bool FA, typename C>
 __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restrict__ tw, C (&v)[16]) {
     using P = Pow2<N>;
     constexpr int Rp = P::radix(S - 1);
     constexpr int Nsp = P::ns(S - 1);
     constexpr int Bp = 16 / Rp;
+    // padded positions: the writes of a butterfly are base + r Nsp with Rp = 16 (only the last
+    // stage has a smaller radix, and it writes nothing); Nsp is 1 or a multiple of 16, so
+    // spad(base + r Nsp) = spad(base) + r (Nsp + Nsp / 16) (for Nsp = 1, base is a multiple of
+    // 16 and r < 16): one base address per butterfly plus compile-time offsets
+    static_assert(Rp == 16, "only the last stage has a radix below 16");
+    static_assert(Nsp == 1 || Nsp % 16 == 0, "Ns is a power of 16");
+    constexpr int WSTEP = Nsp == 1 ? 1 : Nsp + Nsp / 16;
 #pragma unroll
     for (int u = 0; u < Bp; ++u) {
         const int j = t + P::G * u;
         const int base = (j / Nsp) * Nsp * Rp + (j % Nsp);
+        if constexpr (FA) {
+            C* dst = sm + spad(base) * W + c;
 #pragma unroll
-        for (int r = 0; r < Rp; ++r) sm[spad(base + r * Nsp) * W + c] = v[u * Rp + r];
+            for (int r = 0; r < Rp; ++r) dst[r * WSTEP * W] = v[u * Rp + r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < Rp; ++r) sm[spad(base + r * Nsp) * W + c] = v[u * Rp + r];
+        }
     }
     __syncthreads();
     constexpr int R = P::radix(S);
@@ -58,10 +74,15 @@ __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restri
     constexpr int B = 16 / R;
     constexpr int NR = N / R;
     constexpr int TS = N / (Ns * R);
+    // reads j + r NR, NR = N / R a multiple of 16: spad(j) + r (NR + NR / 16)
+    static_assert(NR % 16 == 0, "stage stride a multiple of the padding period");
+    constexpr int RSTEP = NR + NR / 16;
 #pragma unroll
     for (int u = 0; u < B; ++u) {
         const int j = t + P::G * u;
         const int k = j % Ns;
+        const C* src = sm + spad(j) * W + c;
+        auto rd = [&](int r) -> C { return FA ? src[r * RSTEP * W] : sm[spad(j + r * NR) * W + c]; };
         if constexpr (sizeof(C) == 8) {
             // float: one first-order twiddle w = exp(DIR 2 pi i k / (Ns R)) per butterfly, from the
             // base table (stride 1) or the stage's compact table; w^r by a product tree of depth
@@ -73,13 +94,13 @@ __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restri
             for (int r = 2; r < R; ++r) wp[r] = cmul(wp[r / 2], wp[r - r / 2]);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const C x = sm[spad(j + r * NR) * W + c];
+                const C x = rd(r);
                 v[u * R + r] = r > 0 ? cmul(x, wp[r]) : x;
             }
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                C x = sm[spad(j + r * NR) * W + c];
+                C x = rd(r);
                 if (r > 0) {
                     C w = __ldg(tw + r * k * TS);
                     if (DIR > 0) w.y = -w.y;
@@ -92,7 +113,7 @@ __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restri
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < B; ++u) dft_small<R, DIR>(v + u * R);
-    if constexpr (S + 1 < P::NST) p2_stages<N, DIR, W, S + 1>(c, t, sm, tw, v);
+    if constexpr (S + 1 < P::NST) p2_stages<N, DIR, W, S + 1, FA>(c, t, sm, tw, v);
 }
 
 // Twiddle table of a length-N transform (built on the host): tw[e] = exp(-2 pi i e / N) for
@@ -101,13 +122,13 @@ __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restri
 // ranges [N + Ns, N + 2 Ns) are disjoint and end below 2 N.
 // Full transform: v receives the outputs (positions from p2_out_pos).  All threads of the
 // block must call it (it synchronises the block); `sm` holds Pow2<N>::SMEM * W elements.
-template <int N, int DIR, int W, typename C, class Load>
+template <int N, int DIR, int W, bool FA = true, typename C, class Load>
 __device__ __forceinline__ void fft_p2(int c, int t, C* sm, const C* __restrict__ tw, Load&& load, C (&v)[16]) {
     using P = Pow2<N>;
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = load(t + r * P::G);
     dft16<DIR>(v);
-    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1>(c, t, sm, tw, v);
+    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1, FA>(c, t, sm, tw, v);
 }
 
 // Register m of thread t holds element t + G m: the order stage 0 reads its inputs in.  The
@@ -119,11 +140,11 @@ template <int N> __host__ __device__ constexpr int p2_out_m(int idx) {
 }
 
 // Full transform of the 16 values already in registers (v[m] = element t + G m).
-template <int N, int DIR, int W, typename C>
+template <int N, int DIR, int W, bool FA = true, typename C>
 __device__ __forceinline__ void fft_p2_regs(int c, int t, C* sm, const C* __restrict__ tw, C (&v)[16]) {
     using P = Pow2<N>;
     dft16<DIR>(v);
-    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1>(c, t, sm, tw, v);
+    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1, FA>(c, t, sm, tw, v);
 }
 
 }  // namespace dgt

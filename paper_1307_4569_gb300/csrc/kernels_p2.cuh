@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS) fft_prod_adj_p2(const c
         for (int64_t w = 0; w < g.q; ++w) {
             const C* yb = y + ((b * J + j) * g.d * g.q + w) * g.M + k;
             C v[16];
-            fft_p2<N, -1, CF::W>(c, t, sm, tw, [&](int nu) -> C {
+            fft_p2<N, -1, CF::W, false>(c, t, sm, tw, [&](int nu) -> C {
                 return ok ? yb[(int64_t)g.q * nu * g.M] : mk((T)0, (T)0);
             }, v);
             int64_t colG = k - g.a * w;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_prod_ifft_p2(const 
     C zfm[16];
     {
         C v[16];
-        fft_p2<N, -1, CF::W>(c, t, sm, tw, [&](int e) -> C {
+        fft_p2<N, -1, CF::W, false>(c, t, sm, tw, [&](int e) -> C {
             if (!ok) return mk((T)0, (T)0);
             const int64_t l = k + K0 * e;
             C x = load_any<C>(src, src_real, b * sbs + l);
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_prod_ifft_p2(const 
                 if (wrap) x = cmulc(x, __ldg(tw + xi));
                 v[m] = x;
             }
-            fft_p2_regs<N, +1, CF::W>(c, t, sm, tw, v);
+            fft_p2_regs<N, +1, CF::W, false>(c, t, sm, tw, v);
             if (ok) {
                 C* yb = y + ((b * J + j) * g.d * g.q + w) * g.M + k;
 #pragma unroll
