@@ -362,7 +362,10 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
 // FIR analysis: h_n(k) gathered straight from the signal, FFT over k, store column n of c.
 // Sample l = ln + t (tap t of column n) enters with the modulated tap mtaps[wn][t]; the
 // column constant exp(-2 pi i ln wn / (lam2 M)) multiplies the transformed column.
-template <typename T, int N, bool MULTI>
+// SEG: the RPB columns of a CTA are consecutive columns of one signal; their common segment
+// of (RPB - 1) a + Lg samples is first copied to shared memory with coalesced loads, and the
+// taps are gathered from there.
+template <typename T, int N, bool MULTI, bool SEG>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void* __restrict__ f, int f_real,
                                                                       cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
                                                                       int64_t rows_total,
@@ -384,30 +387,67 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
     const T* fr = reinterpret_cast<const T*>(f) + b * fp.L;
     const C* fc = reinterpret_cast<const C*>(f) + b * fp.L;
     const C ph = wn ? fp.cisLM(-(ln * wn)) : mk((T)1, (T)0);       // column constant
-    auto tap_value = [&](int tap) -> C {
-        int64_t l = ln + tap;
-        if (l >= fp.L) l -= fp.L;
-        const C m = __ldg(mt + tap);
-        if (f_real) {
-            const T x = fr[l];
-            return mk(x * m.x, x * m.y);
-        }
-        return cmul(fc[l], m);
-    };
     C v[16];
-    if constexpr (!MULTI) {
-        // Lg <= N: at most one tap per bin, straight-line loads
+    if constexpr (SEG) {
+        // segment of the CTA's first column: samples ln0 + i, i < S (S <= L, host-checked)
+        unsigned char* segp = smem_raw + sizeof(C) * (size_t)Pow2<N>::SMEM * RC::RPB;
+        const int S = (RC::RPB - 1) * (int)fp.a + Lg;
+        int64_t ln0 = ln - (int64_t)gi * fp.a;                   // all columns of the CTA are valid
+        if (ln0 < 0) ln0 += fp.L;
+        if (f_real) {
+            T* seg = reinterpret_cast<T*>(segp);
+            for (int i = threadIdx.x; i < S; i += RC::THREADS) {
+                int64_t l = ln0 + i;
+                if (l >= fp.L) l -= fp.L;
+                seg[i] = fr[l];
+            }
+        } else {
+            C* seg = reinterpret_cast<C*>(segp);
+            for (int i = threadIdx.x; i < S; i += RC::THREADS) {
+                int64_t l = ln0 + i;
+                if (l >= fp.L) l -= fp.L;
+                seg[i] = fc[l];
+            }
+        }
+        __syncthreads();
+        const int off = gi * (int)fp.a;
+        const T* segr = reinterpret_cast<const T*>(segp) + off;
+        const C* segc = reinterpret_cast<const C*>(segp) + off;
         fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
             const int tap = (k - lnm) & (N - 1);
-            return (ok && tap < Lg) ? tap_value(tap) : mk((T)0, (T)0);
+            if (tap >= Lg) return mk((T)0, (T)0);
+            const C m = __ldg(mt + tap);
+            if (f_real) {
+                const T x = segr[tap];
+                return mk(x * m.x, x * m.y);
+            }
+            return cmul(segc[tap], m);
         }, v);
     } else {
-        fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
-            C h = mk((T)0, (T)0);
-            if (!ok) return h;
-            for (int tap = (k - lnm) & (N - 1); tap < Lg; tap += N) h = cadd(h, tap_value(tap));
-            return h;
-        }, v);
+        auto tap_value = [&](int tap) -> C {
+            int64_t l = ln + tap;
+            if (l >= fp.L) l -= fp.L;
+            const C m = __ldg(mt + tap);
+            if (f_real) {
+                const T x = fr[l];
+                return mk(x * m.x, x * m.y);
+            }
+            return cmul(fc[l], m);
+        };
+        if constexpr (!MULTI) {
+            // Lg <= N: at most one tap per bin, straight-line loads
+            fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
+                const int tap = (k - lnm) & (N - 1);
+                return (ok && tap < Lg) ? tap_value(tap) : mk((T)0, (T)0);
+            }, v);
+        } else {
+            fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
+                C h = mk((T)0, (T)0);
+                if (!ok) return h;
+                for (int tap = (k - lnm) & (N - 1); tap < Lg; tap += N) h = cadd(h, tap_value(tap));
+                return h;
+            }, v);
+        }
     }
     if (!ok) return;
     C* cr = c + row * N;
@@ -611,8 +651,14 @@ template <typename T, int N>
 cudaError_t p2_fir_analysis_n(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp, const void* tw,
                               int64_t B, cudaStream_t st) {
     using RC = RowCfg<N>;
-    const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
-    auto k = fp.Lg > N ? fir_analysis_p2<T, N, true> : fir_analysis_p2<T, N, false>;
+    size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
+    // staged segment: every CTA's columns in one signal, the segment shorter than the signal
+    const int64_t S = (RC::RPB - 1) * fp.a + fp.Lg;
+    const size_t segb = (f_real ? sizeof(T) : sizeof(cplx<T>)) * (size_t)S;
+    const bool seg = fp.Lg <= N && fp.N % RC::RPB == 0 && S <= fp.L && smem + segb <= kSmemBudget;
+    auto k = fp.Lg > N ? fir_analysis_p2<T, N, true, false>
+                       : seg ? fir_analysis_p2<T, N, false, true> : fir_analysis_p2<T, N, false, false>;
+    if (seg) smem += segb;
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     const int64_t rows = B * fp.N;
