@@ -476,7 +476,7 @@ def run_serve(seconds, rate=2000.0, cap_bytes=40 << 30, seed=4, infeasible_every
     from workloads import serve_requests
 
     reqs = serve_requests(rate, seconds, seed=seed, infeasible_every=infeasible_every)
-    ex = GpuExecutor("f32")
+    ex = GpuExecutor("f32", streams=4, arena_bytes=cap_bytes // 4)
     keys = sorted({request_key(r) for r in reqs if r.feasible})
     t0 = time.time()
     ex.warm(keys)

@@ -124,6 +124,8 @@ class Scheduler:
 
     def _run(self, requests, clock, idle) -> ServeStats:
         order = sorted(range(len(requests)), key=lambda i: requests[i].t_arrival)
+        # executors with fixed per-batch buffers bound a single batch as well
+        per_batch = getattr(self.ex, "max_batch_bytes", None) or self.cap
         stats = ServeStats(served=[Served(i, requests[i].t_arrival) for i in range(len(requests))])
         groups: "collections.OrderedDict[tuple, collections.deque]" = collections.OrderedDict()
         inflight = []                      # (handle, [rid], bytes, batch index)
@@ -177,10 +179,11 @@ class Scheduler:
                 key, kind = gk
                 q = groups[gk]
                 n = min(len(q), self.max_batch)
-                while n > 0 and inflight_bytes + self.ex.bytes_for(key, kind, n) > self.cap:
+                while n > 0 and (inflight_bytes + self.ex.bytes_for(key, kind, n) > self.cap
+                                 or self.ex.bytes_for(key, kind, n) > per_batch):
                     n -= 1
                 if n == 0:
-                    if self.ex.bytes_for(key, kind, 1) > self.cap:
+                    if self.ex.bytes_for(key, kind, 1) > min(self.cap, per_batch):
                         rid = q.popleft()
                         s = stats.served[rid]
                         s.status, s.error, s.t_done = "rejected", "request larger than the admission cap", clock() - t0
@@ -235,7 +238,7 @@ class GpuExecutor:
     keep_results is set (for checks)."""
 
     def __init__(self, precision: str = "f32", pool: int = 2, seed: int = 4, keep_results: bool = False,
-                 device=None, streams: int = 4):
+                 device=None, streams: int = 4, arena_bytes: int = 0):
         import torch
 
         self.torch = torch
@@ -245,6 +248,12 @@ class GpuExecutor:
         self.stream = torch.cuda.Stream(self.dev)              # plan set-up
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(streams)]
         self.free = list(range(streams))
+        # one device arena per stream, allocated once: a batch carves its input, output and
+        # workspace from its stream's arena, so the serving loop never calls the allocator
+        # (a cudaMalloc inside the loop stalls every request queued behind it)
+        self.arenas = [torch.empty(arena_bytes, dtype=torch.uint8, device=self.dev) for _ in range(streams)] \
+            if arena_bytes > 0 else None
+        self.max_batch_bytes = arena_bytes if arena_bytes > 0 else None
         self.pool = pool
         self.seed = seed
         self.keep = keep_results
@@ -286,7 +295,7 @@ class GpuExecutor:
         p = self.plans[key]
         esz = 8 if self.precision == "f32" else 16
         L, a, M = key[0], key[1], key[2]
-        return n * esz * (L + (L // a) * M) + p.workspace_bytes(n)
+        return n * esz * (L + (L // a) * M) + p.workspace_bytes(n) + 3 * 256      # + arena alignment
 
     def _input(self, key, kind, i):
         shp = self._shape(key, kind)
@@ -327,17 +336,30 @@ class GpuExecutor:
             self.free.append(si)
             raise
 
+    def _buffers(self, si, p, kind, n, L, N, M):
+        torch = self.torch
+        xs, ys = ((n, L), (n, N, M)) if kind == "dgt" else ((n, N, M), (n, L))
+        wsb = max(1, p.workspace_bytes(n))
+        if self.arenas is None:
+            return (torch.empty(xs, dtype=self.cdtype, device=self.dev),
+                    torch.empty(ys, dtype=self.cdtype, device=self.dev),
+                    torch.empty(wsb, dtype=torch.uint8, device=self.dev))
+        esz = 8 if self.precision == "f32" else 16
+        al = lambda v: (v + 255) // 256 * 256
+        nx, ny = esz * int(np.prod(xs)), esz * int(np.prod(ys))
+        if al(nx) + al(ny) + al(wsb) > self.arenas[si].numel():
+            raise RuntimeError("batch of %d does not fit the stream arena" % n)
+        a = self.arenas[si]
+        x = a[:nx].view(self.cdtype).view(xs)
+        y = a[al(nx):al(nx) + ny].view(self.cdtype).view(ys)
+        ws = a[al(nx) + al(ny):al(nx) + al(ny) + wsb]
+        return x, y, ws
+
     def _launch_on(self, si, p, key, kind, n, L, N, M, rids):
         torch = self.torch
         st = self.streams[si]
         with torch.cuda.stream(st):
-            ws = torch.empty(max(1, p.workspace_bytes(n)), dtype=torch.uint8, device=self.dev)
-            if kind == "dgt":
-                x = torch.empty((n, L), dtype=self.cdtype, device=self.dev)
-                y = torch.empty((n, N, M), dtype=self.cdtype, device=self.dev)
-            else:
-                x = torch.empty((n, N, M), dtype=self.cdtype, device=self.dev)
-                y = torch.empty((n, L), dtype=self.cdtype, device=self.dev)
+            x, y, ws = self._buffers(si, p, kind, n, L, N, M)
             for i, rid in enumerate(rids):
                 x[i].copy_(self._input(key, kind, rid), non_blocking=True)
             if kind == "dgt":

@@ -57,7 +57,7 @@ def test_serve_mixed_equals_alone_and_oracle():
     from paper_1307_4569_gb300.serve import GpuExecutor, Scheduler, request_key
 
     reqs = _stream()
-    ex = GpuExecutor("f32", keep_results=True, streams=3)
+    ex = GpuExecutor("f32", keep_results=True, streams=3, arena_bytes=1 << 30)
     st = Scheduler(ex, cap_bytes=8 << 30, max_batch=8, max_inflight=3).run(reqs)
     s = st.summary()
     assert s["errors"] == sum(not r.feasible for r in reqs)

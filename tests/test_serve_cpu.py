@@ -176,3 +176,18 @@ def test_batch_one_serves_everything(max_batch):
     st, ex = _run(reqs, max_batch=max_batch)
     assert all(len(r) <= max_batch for _, _, r in ex.launched)
     assert st.summary()["ok"] == sum(r.feasible for r in reqs)
+
+
+def test_per_batch_limit_of_fixed_buffers():
+    # an executor with fixed per-stream buffers bounds each batch: batches shrink to fit, and
+    # requests that cannot fit one buffer are rejected even though the global cap is large
+    reqs = serve_requests(20000, 0.1, seed=10)
+    clk = SimClock()
+    ex = FakeExecutor(clk, t_req=200e-6)
+    ex.max_batch_bytes = 40 << 20
+    st = Scheduler(ex, 40 << 30, max_batch=64).run(reqs, clock=clk, idle=clk.idle)
+    for key, kind, rids in ex.launched:
+        assert ex.bytes_for(key, kind, len(rids)) <= ex.max_batch_bytes
+    big = [i for i, r in enumerate(reqs) if r.feasible and ex.bytes_for(
+        (r.L, r.a, r.M, r.lam1, r.lam2, r.window), r.kind, 1) > ex.max_batch_bytes]
+    assert big and all(st.served[i].status == "rejected" for i in big)
