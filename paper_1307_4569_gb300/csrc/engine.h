@@ -177,6 +177,8 @@ cudaError_t p2_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx
 template <typename T>
 cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
                        const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
+// columns per chunk of the power-of-two FIR synthesis for FFT length M (0: not applicable)
+template <typename T> int64_t p2_fir_synthesis_cols(int64_t M, int64_t N, int64_t a, int64_t Lg);
 // lengths of the power-of-two column kernels
 inline bool p2_col_len_ok(int64_t n) { return n >= 128 && n <= 8192 && (n & (n - 1)) == 0; }
 // fused Zak analysis (p = 1): zak_fwd + prod_ifft

@@ -206,11 +206,11 @@ cudaError_t launch_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>*
     using C = cplx<T>;
     if (fp.N % fp.cols) return cudaErrorInvalidValue;
     if (fp.a * fp.cols < fp.Lg - fp.a) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(C) * ((size_t)(fp.cols + fp.group) * (fp.M + 1));
-    if (smem > kSmemBudget) return cudaErrorInvalidValue;
     const int64_t nchunks = fp.N / fp.cols;
     cudaError_t e = p2_fir_synthesis<T>(c, f, f_real, seams, fp, fm.tw, B, st);
     if (e == cudaErrorNotSupported) {
+        const size_t smem = sizeof(C) * ((size_t)(fp.cols + fp.group) * (fp.M + 1));
+        if (smem > kSmemBudget) return cudaErrorInvalidValue;
         auto k = fir_synthesis_kernel<T>;
         e = prep_smem2(k, smem);
         if (e != cudaSuccess) return e;

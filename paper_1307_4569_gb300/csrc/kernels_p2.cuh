@@ -7,6 +7,8 @@
 // touches W consecutive elements of a row.  Row kernels transform contiguous rows: RPB rows
 // per CTA, N/16 threads each.
 #pragma once
+#include <type_traits>
+
 #include "fft_p2.cuh"
 #include "kcommon.cuh"
 
@@ -460,82 +462,96 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
     }
 }
 
-// FIR synthesis: inverse FFT of the chunk's columns into shared rows, each multiplied by the
-// conjugate column constant exp(+2 pi i ln wn / (lam2 M)); then every sample l = ln + t of
-// the chunk's segment gathers f(l) = sum_n conj(mtaps[wn][t]) row_n[l mod M], with the seams
-// of the generic kernel (fir_synthesis_kernel).
-template <int N> struct SynCfg {
+// FIR synthesis: per chunk of `cols` consecutive columns, the inverse FFT of each column (times
+// the conjugate column constant exp(+2 pi i ln wn / (lam2 M))) is scattered straight from the
+// registers into a shared accumulator of the chunk's segment of a (cols - 1) + Lg samples:
+// f(ln + t) += row_n[(ln + t) mod M] conj(mtaps[wn][t]).  Columns D = ceil(Lg / a) apart never
+// touch the same sample, so the columns are taken in D rounds (r = q, q + D, ...): within a
+// round no two columns collide, and a barrier separates the rounds.  Real output accumulates
+// the real part only.  The first and last Lg - a samples of the segment, shared with the
+// neighbouring chunks, go to the seam buffer (fir_seams sums them); Lg <= M (one tap per bin).
+// RPB columns are transformed at once (RPB groups of N/16 threads): the largest count for 512
+// threads, or a quarter of it where the wider tiles of a larger element do not fit otherwise
+template <int N, int DIV = 1> struct SynCfg {
     static constexpr int G = N / 16;
-    static constexpr int RPB = G >= 512 ? 1 : 512 / G;                    // rows transformed at once
+    static constexpr int RPB0 = G >= 512 ? 1 : 512 / G;
+    static constexpr int RPB = RPB0 / DIV > 0 ? RPB0 / DIV : 1;
     static constexpr int THREADS = RPB * G;
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(SynCfg<N>::THREADS) fir_synthesis_p2(const cplx<T>* __restrict__ c,
-                                                                       void* __restrict__ f, int f_real,
+template <typename T, int N, bool REAL, int DIV>
+__global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_p2(const cplx<T>* __restrict__ c,
+                                                                       void* __restrict__ f,
                                                                        cplx<T>* __restrict__ seams,
                                                                        FirParams<cplx<T>> fp,
                                                                        const cplx<T>* __restrict__ tw) {
     using C = cplx<T>;
-    using RC = SynCfg<N>;
+    using A = typename std::conditional<REAL, T, C>::type;
+    using RC = SynCfg<N, DIV>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int SM = Pow2<N>::SMEM;
-    C* rows = reinterpret_cast<C*>(smem_raw);           // cols rows of SM elements (padded index)
+    C* sm = reinterpret_cast<C*>(smem_raw) + (threadIdx.x / RC::G) * Pow2<N>::SMEM;
+    A* acc = reinterpret_cast<A*>(smem_raw + sizeof(C) * (size_t)Pow2<N>::SMEM * RC::RPB);
     const int gi = threadIdx.x / RC::G, t = threadIdx.x % RC::G;
     const int64_t b = blockIdx.y;
     const int64_t chunk = blockIdx.x;
     const int64_t nchunks = gridDim.x;
     const int64_t n0 = chunk * fp.cols;
     const int nc = (int)fp.cols;
-    const int lam2 = (int)fp.lam2;
-    // per column: offset wn Lg of its modulated taps, wn = (n lam1) mod lam2
-    __shared__ int s_mt[64];
-    for (int r = threadIdx.x; r < nc; r += blockDim.x) s_mt[r] = (int)(((n0 + r) * fp.lam1) % lam2) * (int)fp.Lg;
+    const int a = (int)fp.a, Lg = (int)fp.Lg;
+    const int S = a * (nc - 1) + Lg;
+    const int D = (Lg + a - 1) / a;                  // columns closer than D overlap
+    const int PR = nc / D;                           // columns per round (nc % D == 0, host-checked)
+    for (int i = threadIdx.x; i < S; i += RC::THREADS) {
+        if constexpr (REAL) acc[i] = (T)0;
+        else acc[i] = mk((T)0, (T)0);
+    }
     __syncthreads();
-    for (int r0 = 0; r0 < nc; r0 += RC::RPB) {
-        const int r = r0 + gi;
-        const bool ok = r < nc;
-        C* sm = rows + (ok ? r : nc) * SM;                  // row nc is a spare row for idle groups
-        const C* cr = c + (b * fp.N + n0 + (ok ? r : 0)) * fp.M;
-        C v[16];
-        fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C { return ok ? cr[m] : mk((T)0, (T)0); }, v);
-        if (ok) {
-            const int64_t n = n0 + r;
-            const int wn = (int)((n * fp.lam1) % lam2);
-            if (wn) {
+    for (int q = 0; q < D; ++q) {
+        for (int s0 = 0; s0 < PR; s0 += RC::RPB) {
+            const int sidx = s0 + gi;
+            const bool ok = sidx < PR;
+            const int r = q + D * sidx;
+            const int64_t n = n0 + (ok ? r : 0);
+            const C* cr = c + (b * fp.N + n) * fp.M;
+            C v[16];
+            fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C { return ok ? cr[m] : mk((T)0, (T)0); }, v);
+            if (ok) {
+                const int wn = (int)((n * fp.lam1) % fp.lam2);
                 int64_t ln = fp.a * n - fp.center;
                 if (ln < 0) ln += fp.L;
-                const C ph = fp.cisLM(ln * wn);
+                const int lnm = (int)(ln & (N - 1));
+                const C ph = wn ? fp.cisLM(ln * wn) : mk((T)1, (T)0);
+                const C* mt = fp.mtaps + (int64_t)wn * Lg;
+                A* ar = acc + r * a;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) sm[spad(p2_out_pos<N>(t, i))] = cmul(v[i], ph);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) sm[spad(p2_out_pos<N>(t, i))] = v[i];
+                for (int i = 0; i < 16; ++i) {
+                    const int tap = (p2_out_pos<N>(t, i) - lnm) & (N - 1);
+                    if (tap < Lg) {
+                        const C u = wn ? cmul(v[i], ph) : v[i];
+                        const C m = __ldg(mt + tap);
+                        if constexpr (REAL) ar[tap] += u.x * m.x + u.y * m.y;
+                        else ar[tap] = cadd(ar[tap], cmulc(u, m));
+                    }
+                }
             }
         }
-        __syncthreads();
+        __syncthreads();                            // the next round's columns overlap these
     }
-    const int64_t S = fp.a * (nc - 1) + fp.Lg;
-    const int64_t ov = fp.Lg > fp.a ? fp.Lg - fp.a : 0;
+    const int ov = Lg > a ? Lg - a : 0;
     int64_t lstart = fp.a * n0 - fp.center;
     if (lstart < 0) lstart += fp.L;
     C* seamL = seams + (b * nchunks + chunk) * 2 * ov;
     C* seamR = seamL + ov;
-    const int a = (int)fp.a, Lg = (int)fp.Lg;
-    for (int tt = threadIdx.x; tt < (int)S; tt += blockDim.x) {
+    for (int tt = threadIdx.x; tt < S; tt += RC::THREADS) {
         int64_t l = lstart + tt;
         if (l >= fp.L) l -= fp.L;
-        const int km = (int)(l & (N - 1));
-        C acc = mk((T)0, (T)0);
-        const int rlo = tt - Lg + 1 <= 0 ? 0 : (tt - Lg + a) / a;
-        const int rhi = min(nc - 1, tt / a);
-        for (int r = rlo; r <= rhi; ++r) {
-            const int tap = tt - a * r;
-            acc = cadd(acc, cmulc(rows[r * SM + spad(km)], __ldg(fp.mtaps + s_mt[r] + tap)));
-        }
-        if (tt < ov) seamL[tt] = acc;
-        else if (tt >= S - ov) seamR[tt - (S - ov)] = acc;
-        else store_any(f, f_real, b * fp.L + l, acc);
+        C val;
+        if constexpr (REAL) val = mk(acc[tt], (T)0);
+        else val = acc[tt];
+        if (tt < ov) seamL[tt] = val;
+        else if (tt >= S - ov) seamR[tt - (S - ov)] = val;
+        else if constexpr (REAL) reinterpret_cast<T*>(f)[b * fp.L + l] = val.x;
+        else reinterpret_cast<C*>(f)[b * fp.L + l] = val;
     }
 }
 
@@ -667,18 +683,55 @@ cudaError_t p2_fir_analysis_n(const void* f, int f_real, cplx<T>* c, const FirPa
     return cudaGetLastError();
 }
 
-template <typename T, int N>
-cudaError_t p2_fir_synthesis_n(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
-                               const void* tw, int64_t B, cudaStream_t st) {
-    using RC = SynCfg<N>;
-    const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * (fp.cols + 1);
-    if (smem > kSmemBudget + 16 * 1024) return cudaErrorNotSupported;
-    auto k = fir_synthesis_p2<T, N>;
+// shared bytes of the FIR synthesis kernel for `cols` columns per chunk
+template <typename T, int N, int DIV> size_t p2_fir_synthesis_smem(int64_t cols, int64_t a, int64_t Lg, int f_real) {
+    return sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * SynCfg<N, DIV>::RPB +
+           (f_real ? sizeof(T) : sizeof(cplx<T>)) * (size_t)(a * (cols - 1) + Lg);
+}
+
+// a chunk of `cols` columns suits the variant DIV: rounds of cols / D columns fill whole
+// batches of RPB transforms, and the tile (complex accumulator) fits
+template <typename T, int N, int DIV> bool p2_fir_synthesis_fits(int64_t cols, int64_t Nn, int64_t a, int64_t Lg) {
+    const int64_t D = (Lg + a - 1) / a;
+    return Lg <= N && cols % D == 0 && Nn % cols == 0 && (cols / D) % SynCfg<N, DIV>::RPB == 0 &&
+           p2_fir_synthesis_smem<T, N, DIV>(cols, a, Lg, 0) <= kSmemBudget;
+}
+
+template <typename T, int N, int DIV>
+cudaError_t p2_fir_synthesis_launch(const cplx<T>* c, void* f, int f_real, cplx<T>* seams,
+                                    const FirParams<cplx<T>>& fp, const void* tw, int64_t B, cudaStream_t st) {
+    const size_t smem = p2_fir_synthesis_smem<T, N, DIV>(fp.cols, fp.a, fp.Lg, f_real);
+    auto k = f_real ? fir_synthesis_p2<T, N, true, DIV> : fir_synthesis_p2<T, N, false, DIV>;
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(fp.N / fp.cols), (unsigned)B);
-    k<<<grid, RC::THREADS, smem, st>>>(c, f, f_real, seams, fp, (const cplx<T>*)tw);
+    k<<<grid, SynCfg<N, DIV>::THREADS, smem, st>>>(c, f, seams, fp, (const cplx<T>*)tw);
     return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t p2_fir_synthesis_n(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
+                               const void* tw, int64_t B, cudaStream_t st) {
+    if (p2_fir_synthesis_fits<T, N, 1>(fp.cols, fp.N, fp.a, fp.Lg))
+        return p2_fir_synthesis_launch<T, N, 1>(c, f, f_real, seams, fp, tw, B, st);
+    if (p2_fir_synthesis_fits<T, N, 4>(fp.cols, fp.N, fp.a, fp.Lg))
+        return p2_fir_synthesis_launch<T, N, 4>(c, f, f_real, seams, fp, tw, B, st);
+    return cudaErrorNotSupported;
+}
+
+// columns per chunk for the power-of-two FIR synthesis: the widest chunk (fewest seams) that
+// the full-width variant takes, else the widest for the quarter-width one; 0 when neither
+// applies (the generic kernel runs)
+template <typename T, int N> int64_t p2_fir_synthesis_cols_n(int64_t Nn, int64_t a, int64_t Lg) {
+    if (Lg > N) return 0;
+    const int64_t D = (Lg + a - 1) / a;
+    int64_t best = 0;
+    for (int64_t cols = D; cols <= 256; cols += D)
+        if (p2_fir_synthesis_fits<T, N, 1>(cols, Nn, a, Lg)) best = cols;
+    if (best) return best;
+    for (int64_t cols = D; cols <= 256; cols += D)
+        if (p2_fir_synthesis_fits<T, N, 4>(cols, Nn, a, Lg)) best = cols;
+    return best;
 }
 
 template <typename T, int N>
@@ -740,6 +793,19 @@ template <typename T>
 cudaError_t p2_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp, const void* tw,
                             int64_t B, cudaStream_t st) {
     P2_SWITCH(fp.M, return (p2_fir_analysis_n<T, NN>(f, f_real, c, fp, tw, B, st)))
+}
+template <typename T>
+int64_t p2_fir_synthesis_cols(int64_t M, int64_t Nn, int64_t a, int64_t Lg) {
+    switch (M) {
+        case 128: return p2_fir_synthesis_cols_n<T, 128>(Nn, a, Lg);
+        case 256: return p2_fir_synthesis_cols_n<T, 256>(Nn, a, Lg);
+        case 512: return p2_fir_synthesis_cols_n<T, 512>(Nn, a, Lg);
+        case 1024: return p2_fir_synthesis_cols_n<T, 1024>(Nn, a, Lg);
+        case 2048: return p2_fir_synthesis_cols_n<T, 2048>(Nn, a, Lg);
+        case 4096: return p2_fir_synthesis_cols_n<T, 4096>(Nn, a, Lg);
+        case 8192: return p2_fir_synthesis_cols_n<T, 8192>(Nn, a, Lg);
+        default: return 0;
+    }
 }
 template <typename T>
 cudaError_t p2_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,

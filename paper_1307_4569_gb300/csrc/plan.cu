@@ -899,6 +899,14 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
             if (k.N % cc == 0 && group_for(cc)) fir_cols = cc;
         if (fir_cols && !fir_synth_ok) fir_synth_ok = a * fir_cols >= g->len - a;
         fir_group = fir_cols ? group_for(fir_cols) : 1;
+        // power-of-two M: the scatter-accumulate synthesis kernel takes wider chunks
+        const int64_t cols2 = precision == DGT_F64 ? p2_fir_synthesis_cols<double>(M, k.N, a, g->len)
+                                                   : p2_fir_synthesis_cols<float>(M, k.N, a, g->len);
+        if (cols2 > 0) {
+            fir_cols = cols2;
+            fir_synth_ok = true;
+            fir_group = 1;
+        }
     }
     if (route == DGT_ROUTE_AUTO) {
         if (g->kind == DGT_WINDOW_FIR && fir_cols && fir_synth_ok && lam2 <= 8) route = DGT_ROUTE_FIR;

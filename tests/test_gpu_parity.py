@@ -171,7 +171,8 @@ def test_dual_tight_small(params, route):
 # -------------------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("params", [(16384, 128, 1024, 1, 2, 1024), (4096, 16, 128, 1, 2, 128),
-                                    (4096, 32, 256, 1, 4, 256), (1728, 12, 144, 1, 3, 96)])
+                                    (4096, 32, 256, 1, 4, 256), (8192, 32, 256, 1, 4, 128),
+                                    (4096, 16, 256, 1, 2, 96), (1728, 12, 144, 1, 3, 96)])
 def test_fir_route(params, prec):
     Plan = _P()
     L, a, M, l1, l2, Lg = params
