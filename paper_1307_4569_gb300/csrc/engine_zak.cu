@@ -80,7 +80,8 @@ cudaError_t launch_zak_fwd(const void* src, int src_real, int64_t sbs, cplx<T>* 
     const int64_t K0 = L / d;
     const int64_t cap = tile_cap<T>();
     if (d > cap) return cudaErrorInvalidValue;
-    const int W = (int)std::max<int64_t>(1, std::min<int64_t>({cap / d, 16, K0}));
+    // columns per CTA: a tile of about 48 KB (two buffers), so that several CTAs share an SM
+    const int W = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(24 * 1024 / sizeof(C)) / d, 16, K0}));
     const int thr = threads_for(d * W);
     const size_t smem = 2 * sizeof(C) * (size_t)d * W;
     auto k = zak_fwd_kernel<T>;
@@ -147,7 +148,7 @@ cudaError_t launch_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cp
     using C = cplx<T>;
     const int64_t cap = tile_cap<T>();
     if (g.d > cap) return cudaErrorInvalidValue;
-    const int W = (int)std::max<int64_t>(1, std::min<int64_t>({cap / g.d, 16, g.M}));
+    const int W = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(24 * 1024 / sizeof(C)) / g.d, 16, g.M}));
     const int thr = threads_for(g.d * W);
     const size_t smem = 2 * sizeof(C) * (size_t)g.d * W;
     auto k = prod_ifft_kernel<T>;
@@ -175,31 +176,41 @@ __global__ void __launch_bounds__(kThreadsBig) fft_post_kernel(const cplx<T>* __
     const int nr = (int)min((int64_t)R, rows_total - row0);
     const int total = nr * n;
     const int TILE = R * pitch;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int r = e / n, k = e % n;
-        s[r * pitch + k] = y[(row0 + r) * n + k];
-    }
+    (void)total;
+    for (int r = 0; r < nr; ++r)
+        for (int k = threadIdx.x; k < n; k += blockDim.x) s[r * pitch + k] = y[(row0 + r) * n + k];
     __syncthreads();
     s = fft_tile<-1, false>(s, s + TILE, pl, nr, 1, pitch, tw);
     const int64_t Nsep = g.d * g.q;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int r = e / n, m = e % n;
+    for (int r = 0; r < nr; ++r) {
+        // the row's separable indices, once per row
         const int64_t row = row0 + r;
         const int64_t b = row / (J * Nsep);
         const int64_t rem = row - b * J * Nsep;
         const int64_t j = rem / Nsep, nn = rem - j * Nsep;
+        if (pp.mode == POST_SHEAR1) {
+            for (int m = threadIdx.x; m < n; m += blockDim.x) {
+                C ph;
+                const int64_t o = out_index(pp, g, b, j, nn, m, ph);
+                c[o] = cmul(s[r * pitch + m], ph);
+            }
+            continue;
+        }
+        // the other modes: output m of the row lands at o0 + m (rotated cyclically for the
+        // time shear), all with the phase of m = 0
+        C ph;
+        const int64_t o0 = out_index(pp, g, b, j, nn, 0, ph);
         if (pp.mode == POST_SHEAR0) {
             // iterate over the output channel so the store is contiguous
-            C ph;
-            const int64_t o0 = out_index(pp, g, b, j, nn, 0, ph);     // position of m = 0
-            const int64_t rot = o0 - (b * pp.N + nn) * pp.M;
-            int64_t src = m - rot;
-            if (src < 0) src += n;
-            c[(b * pp.N + nn) * pp.M + m] = cmul(s[r * pitch + src], ph);
+            const int64_t base = (b * pp.N + nn) * pp.M;
+            const int rot = (int)(o0 - base);
+            for (int m = threadIdx.x; m < n; m += blockDim.x) {
+                int src = m - rot;
+                if (src < 0) src += n;
+                c[base + m] = cmul(s[r * pitch + src], ph);
+            }
         } else {
-            C ph;
-            const int64_t o = out_index(pp, g, b, j, nn, m, ph);
-            c[o] = cmul(s[r * pitch + m], ph);
+            for (int m = threadIdx.x; m < n; m += blockDim.x) c[o0 + m] = cmul(s[r * pitch + m], ph);
         }
     }
 }
@@ -215,7 +226,8 @@ cudaError_t launch_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int6
     const int64_t n = g.M;
     const int64_t cap = tile_cap<T>();
     if (n + 1 > cap) return cudaErrorInvalidValue;
-    const int R = (int)std::max<int64_t>(1, std::min<int64_t>(cap / (n + 1), 16));
+    // rows per CTA: a tile of about 48 KB (two buffers), so that several CTAs share an SM
+    const int R = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(24 * 1024 / sizeof(C)) / (n + 1), 16));
     const int thr = threads_for(n * R);
     const size_t smem = 2 * sizeof(C) * (size_t)(n + 1) * R;
     auto k = fft_post_kernel<T>;
@@ -243,31 +255,39 @@ __global__ void __launch_bounds__(kThreadsBig) pre_ifft_kernel(const cplx<T>* __
     const int nr = (int)min((int64_t)R, rows_total - row0);
     const int total = nr * n;
     const int64_t Nsep = g.d * g.q;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int r = e / n, m = e % n;
+    (void)total;
+    for (int r = 0; r < nr; ++r) {
+        // the row's separable indices, once per row
         const int64_t row = row0 + r;
         const int64_t b = row / (J * Nsep);
         const int64_t rem = row - b * J * Nsep;
         const int64_t j = rem / Nsep, nn = rem - j * Nsep;
+        if (pp.mode == POST_SHEAR1) {
+            for (int m = threadIdx.x; m < n; m += blockDim.x) {
+                C ph;
+                const int64_t o = out_index(pp, g, b, j, nn, m, ph);
+                s[r * pitch + m] = cmulc(c[o], ph);
+            }
+            continue;
+        }
+        C ph;
+        const int64_t o0 = out_index(pp, g, b, j, nn, 0, ph);
         if (pp.mode == POST_SHEAR0) {
-            C ph;
-            const int64_t o0 = out_index(pp, g, b, j, nn, 0, ph);
-            const int64_t rot = o0 - (b * pp.N + nn) * pp.M;
-            int64_t dst = m - rot;                      // separable channel of output channel m
-            if (dst < 0) dst += n;
-            s[r * pitch + dst] = cmulc(c[(b * pp.N + nn) * pp.M + m], ph);
+            const int64_t base = (b * pp.N + nn) * pp.M;
+            const int rot = (int)(o0 - base);
+            for (int m = threadIdx.x; m < n; m += blockDim.x) {
+                int dst = m - rot;                      // separable channel of output channel m
+                if (dst < 0) dst += n;
+                s[r * pitch + dst] = cmulc(c[base + m], ph);
+            }
         } else {
-            C ph;
-            const int64_t o = out_index(pp, g, b, j, nn, m, ph);
-            s[r * pitch + m] = cmulc(c[o], ph);
+            for (int m = threadIdx.x; m < n; m += blockDim.x) s[r * pitch + m] = cmulc(c[o0 + m], ph);
         }
     }
     __syncthreads();
     const C* res = fft_tile<+1, false>(s, s + R * pitch, pl, nr, 1, pitch, tw);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int r = e / n, k = e % n;
-        y[(row0 + r) * n + k] = res[r * pitch + k];
-    }
+    for (int r = 0; r < nr; ++r)
+        for (int k = threadIdx.x; k < n; k += blockDim.x) y[(row0 + r) * n + k] = res[r * pitch + k];
 }
 
 template <typename T>
@@ -281,7 +301,8 @@ cudaError_t launch_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int6
     const int64_t n = g.M;
     const int64_t cap = tile_cap<T>();
     if (n + 1 > cap) return cudaErrorInvalidValue;
-    const int R = (int)std::max<int64_t>(1, std::min<int64_t>(cap / (n + 1), 16));
+    // rows per CTA: a tile of about 48 KB (two buffers), so that several CTAs share an SM
+    const int R = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(24 * 1024 / sizeof(C)) / (n + 1), 16));
     const int thr = threads_for(n * R);
     const size_t smem = 2 * sizeof(C) * (size_t)(n + 1) * R;
     auto k = pre_ifft_kernel<T>;
@@ -359,7 +380,8 @@ cudaError_t launch_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, 
     using C = cplx<T>;
     // two work tiles d*W plus the accumulator p*d*W
     const int64_t elems = (int64_t)(kSmemBudget / sizeof(C));
-    const int64_t W = std::min<int64_t>({elems / (g.d * (2 + g.p)), 16, g.M});
+    const int64_t W = std::min<int64_t>({std::max<int64_t>(1, (int64_t)(36 * 1024 / sizeof(C)) / (g.d * (2 + g.p))),
+                                         elems / (g.d * (2 + g.p)), 16, g.M});
     if (W < 1) return cudaErrorInvalidValue;
     const int thr = threads_for(g.d * W);
     const size_t smem = sizeof(C) * (size_t)g.d * W * (2 + g.p);
@@ -484,7 +506,8 @@ cudaError_t launch_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_re
     const int64_t K0 = L / d;
     const int64_t cap = tile_cap<T>();
     if (d > cap) return cudaErrorInvalidValue;
-    const int W = (int)std::max<int64_t>(1, std::min<int64_t>({cap / d, 16, K0}));
+    // columns per CTA: a tile of about 48 KB (two buffers), so that several CTAs share an SM
+    const int W = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(24 * 1024 / sizeof(C)) / d, 16, K0}));
     const int thr = threads_for(d * W);
     const size_t smem = 2 * sizeof(C) * (size_t)d * W;
     auto k = zak_inv_kernel<T>;
@@ -631,7 +654,8 @@ cudaError_t launch_fft_rows_test(const cplx<T>* in, cplx<T>* out, const FftRef& 
     const int64_t n = f.pl.n;
     const int64_t cap = tile_cap<T>();
     if (n + 1 > cap) return cudaErrorInvalidValue;
-    const int R = (int)std::max<int64_t>(1, std::min<int64_t>(cap / (n + 1), 16));
+    // rows per CTA: a tile of about 48 KB (two buffers), so that several CTAs share an SM
+    const int R = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(24 * 1024 / sizeof(C)) / (n + 1), 16));
     const int thr = threads_for(n * R);
     const size_t smem = 2 * sizeof(C) * (size_t)(n + 1) * R;
     auto k = fft_rows_test_kernel<T>;

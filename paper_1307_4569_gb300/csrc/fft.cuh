@@ -178,14 +178,26 @@ template <int R, int DIR, bool BATCH_FAST, typename C>
 __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst, int n, int nb, int es,
                                                int bs, int Ns, const C* __restrict__ tw) {
     const int nbf = n / R;
-    const int total = nbf * nb;
     const int tstride = n / (Ns * R);
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int t, j;
-        if (BATCH_FAST) { t = idx % nb; j = idx / nb; } else { j = idx % nbf; t = idx / nbf; }
+    // butterfly (t, j), j = jq Ns + k: the thread's first index is split once with divisions,
+    // then advanced by the block size with adds and carries only (nbf is a multiple of Ns)
+    const int T = blockDim.x;
+    const int idx0 = threadIdx.x;
+    int t, j;
+    int dt, dj;                              // the block step split like an index
+    if (BATCH_FAST) {
+        t = idx0 % nb; j = idx0 / nb;
+        dt = T % nb; dj = T / nb;
+    } else {
+        j = idx0 % nbf; t = idx0 / nbf;
+        dj = T % nbf; dt = T / nbf;
+    }
+    int jq = j / Ns, k = j - jq * Ns;
+    const int djq = dj / Ns, dk = dj - djq * Ns;
+    const int nq = nbf / Ns;
+    for (; BATCH_FAST ? j < nbf : t < nb;) {
         const C* s = src + t * bs;
         C* d = dst + t * bs;
-        const int k = j % Ns;
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -198,9 +210,20 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __r
             v[r] = x;
         }
         dft_small<R, DIR>(v);
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = jq * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) d[(base + r * Ns) * es] = v[r];
+        // advance (t, j) by T
+        if (BATCH_FAST) {
+            t += dt;
+            j += dj; jq += djq; k += dk;
+            if (t >= nb) { t -= nb; ++j; ++k; }
+        } else {
+            j += dj; jq += djq; k += dk;
+            t += dt;
+            if (j >= nbf) { j -= nbf; jq -= nq; ++t; }
+        }
+        if (k >= Ns) { k -= Ns; ++jq; }
     }
 }
 
