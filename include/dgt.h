@@ -85,6 +85,8 @@ typedef struct {
     int64_t c, d, p, q;       /* its constants, eqs. (cd, pq) */
     int64_t n_windows;        /* window factors held (lambda2 for coset, 1 otherwise) */
     int64_t fir_len;          /* FIR taps (FIR route) */
+    int64_t ola_block;        /* blockwise plans: block length Lb (0 otherwise) */
+    int64_t ola_len;          /* blockwise plans: length Lx of the blocks' transforms */
 } dgt_plan_info;
 
 /* Create a plan for the lattice (L, a, M, lambda1/lambda2) and window g.
@@ -94,6 +96,26 @@ typedef struct {
  * Errors: DGT_ERR_ARG, DGT_ERR_LENGTH, DGT_ERR_UNSUPPORTED, DGT_ERR_OOM, DGT_ERR_CUDA. */
 int dgt_plan_create(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t lambda1, int64_t lambda2,
                     const dgt_window* g, int route, int precision, void* stream);
+
+/* Blockwise (overlap-add) plan for an FIR window: Section 3 (the OLA algorithm) and Section 4
+ * (the shear-OLA algorithm).  The signal is cut into L / block_len blocks; each block,
+ * zero-extended to Lx = the smallest multiple of lambda2 * lcm(a, M) not below
+ * block_len + g->len whose transform this build supports (reported as ola_len by
+ * dgt_plan_get_info), is transformed by a full-window plan of length Lx (inner_route:
+ * DGT_ROUTE_COSET, DGT_ROUTE_SHEAR, or DGT_ROUTE_AUTO for shear when s0 = 0, else coset),
+ * and the blocks' coefficient columns are added into the columns of the length-L
+ * transform; synthesis is the adjoint (gather the columns, synthesise each block, keep its
+ * block_len samples).  The results equal those of dgt_plan_create with the same FIR window;
+ * the cost grows by rho = Lx / block_len (eq. OLA-eff).  The handle works with dgt_exec,
+ * dgt_exec_ws, idgt_exec, idgt_exec_ws (adjoint, and dual / tight for windows no longer
+ * than M), dgt_window_dual / _tight (length-L windows), dgt_workspace_bytes, dgt_plan_bytes,
+ * dgt_plan_status, dgt_plan_get_info and dgt_plan_destroy; the other entry points return
+ * DGT_ERR_UNSUPPORTED or DGT_ERR_ARG.  Synchronises `stream`.
+ * Errors: DGT_ERR_ARG (not an FIR window, block shorter than the window, FIR inner route),
+ * DGT_ERR_LENGTH (L or block_len not a multiple of lambda2 * lcm(a, M), block_len not
+ * dividing L, Lx > L), and those of dgt_plan_create for the blocks' plan. */
+int dgt_plan_create_ola(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t lambda1, int64_t lambda2,
+                        const dgt_window* g, int64_t block_len, int inner_route, int precision, void* stream);
 
 /* Copy the resolved plan parameters into *info. */
 int dgt_plan_get_info(dgt_plan_t plan, dgt_plan_info* info);

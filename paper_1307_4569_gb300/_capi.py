@@ -30,7 +30,7 @@ class PlanInfo(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("L", "a", "M", "lambda1", "lambda2", "b", "N", "s")] + \
                [("route", C.c_int), ("precision", C.c_int)] + \
                [(n, C.c_int64) for n in ("s0", "s1", "b_r", "sep_a", "sep_M", "c", "d", "p", "q",
-                                         "n_windows", "fir_len")]
+                                         "n_windows", "fir_len", "ola_block", "ola_len")]
 
 
 class DGTError(RuntimeError):
@@ -47,6 +47,7 @@ _lib = None
 vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
 SIGNATURES = {
     "dgt_plan_create": (i32, [C.POINTER(vp), i64, i64, i64, i64, i64, C.POINTER(Window), i32, i32, vp]),
+    "dgt_plan_create_ola": (i32, [C.POINTER(vp), i64, i64, i64, i64, i64, C.POINTER(Window), i64, i32, i32, vp]),
     "dgt_plan_get_info": (i32, [vp, C.POINTER(PlanInfo)]),
     "dgt_plan_set_window": (i32, [vp, vp, i32, vp]),
     "dgt_exec": (i32, [vp, vp, i32, vp, i64, vp]),

@@ -30,9 +30,13 @@ class Plan:
     window: 1-D numpy array / CPU tensor, real or complex; full length L, or FIR taps
     when `fir_center` is given (tap t sits at time t - fir_center).
     precision: "f32" or "f64".  route: "auto", "coset", "shear" or "fir".
+    block_len: blockwise (overlap-add) plan for an FIR window: blocks of block_len samples
+    transformed by the coset or shear route ("auto", "coset", "shear") on the zero-extended
+    block, the same results as the plain plan (dgt_plan_create_ola).
     """
 
-    def __init__(self, L, a, M, lam1, lam2, window, route="auto", precision="f32", fir_center=None, stream=None):
+    def __init__(self, L, a, M, lam1, lam2, window, route="auto", precision="f32", fir_center=None, stream=None,
+                 block_len=None):
         w = np.asarray(window.detach().cpu().numpy() if torch.is_tensor(window) else window)
         self.is_real_window = not np.iscomplexobj(w)
         data = np.ascontiguousarray(w.astype(np.float64) if self.is_real_window
@@ -43,8 +47,14 @@ class Plan:
         self.precision = precision
         prec = K.F64 if precision == "f64" else K.F32
         h = C.c_void_p()
-        K.check(K.lib().dgt_plan_create(C.byref(h), L, a, M, lam1, lam2, C.byref(win), _ROUTES[route], prec,
-                                         _stream(stream)))
+        if block_len is not None:
+            if fir_center is None:
+                raise ValueError("a blockwise plan needs FIR taps (fir_center)")
+            K.check(K.lib().dgt_plan_create_ola(C.byref(h), L, a, M, lam1, lam2, C.byref(win), int(block_len),
+                                                 _ROUTES[route], prec, _stream(stream)))
+        else:
+            K.check(K.lib().dgt_plan_create(C.byref(h), L, a, M, lam1, lam2, C.byref(win), _ROUTES[route], prec,
+                                             _stream(stream)))
         self._h = h
         info = K.PlanInfo()
         K.check(K.lib().dgt_plan_get_info(self._h, C.byref(info)))

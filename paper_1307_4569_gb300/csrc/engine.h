@@ -134,6 +134,21 @@ int64_t fir_seam_elems(const FirParams<C>& fp);
 template <typename T>
 cudaError_t launch_fir_modtaps(const double2* h, cplx<T>* out, int64_t Lg, int64_t lam2, int64_t M, cudaStream_t st);
 
+// blockwise (overlap-add) DGT: block length Lb, Nb blocks, local length Lx with Nx columns;
+// S = Lb / a global columns per block; local columns 0..nu_hi keep their offset, the rest stand
+// for offset nu - Nx; K = blocks that can reach one global column (at most Nb)
+struct OlaGeom {
+    int64_t L, a, M, N, Lb, Nb, Lx, Nx, S, nu_hi, K;
+};
+template <typename T>
+cudaError_t launch_ola_split(const void* f, int f_real, void* x, const OlaGeom& og, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ola_take(const void* y, int f_real, void* f, const OlaGeom& og, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ola_add(const cplx<T>* cx, cplx<T>* c, const OlaGeom& og, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ola_gather(const cplx<T>* c, cplx<T>* cx, const OlaGeom& og, int64_t B, cudaStream_t st);
+
 // elementwise helpers
 template <typename T>
 cudaError_t launch_coset_windows(const cplx<T>* g, cplx<T>* gj, int64_t L, int64_t a, int64_t J, const int64_t* sigma,

@@ -540,6 +540,106 @@ template cudaError_t launch_fir_modtaps<float>(const double2*, float2*, int64_t,
 template cudaError_t launch_fir_modtaps<double>(const double2*, double2*, int64_t, int64_t, int64_t, cudaStream_t);
 
 // =====================================================================================
+// Blockwise (overlap-add) DGT: block buffers and the column map between the blocks' short
+// transforms (length Lx, Nx = Lx / a columns) and the long one (N columns).  Block beta
+// starts at sample beta Lb; its local column nu' stands for the global column
+// (beta S + nu) mod N, S = Lb / a, nu = nu' for nu' <= nu_hi and nu' - Nx otherwise.
+// =====================================================================================
+template <typename E>
+__global__ void ola_split_kernel(const E* __restrict__ f, E* __restrict__ x, OlaGeom og, int64_t B) {
+    const int64_t total = B * og.Nb * og.Lx;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = e % og.Lx, bb = e / og.Lx;            // bb = b Nb + beta
+        E v{};
+        if (u < og.Lb) v = f[bb * og.Lb + u];                    // block beta of signal b is contiguous
+        x[e] = v;
+    }
+}
+
+template <typename E>
+__global__ void ola_take_kernel(const E* __restrict__ y, E* __restrict__ f, OlaGeom og, int64_t B) {
+    const int64_t total = B * og.Nb * og.Lb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = e % og.Lb, bb = e / og.Lb;
+        f[e] = y[bb * og.Lx + u];
+    }
+}
+
+// c[b][n][m] = sum over the blocks whose columns include n, in increasing distance order
+template <typename C>
+__global__ void ola_add_kernel(const C* __restrict__ cx, C* __restrict__ c, OlaGeom og, int64_t B) {
+    const int64_t total = B * og.N * og.M;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = e % og.M, r = e / og.M;
+        const int64_t n = r % og.N, b = r / og.N;
+        // the latest block that can reach n through a wrapped (negative) local column
+        const int64_t top = (n + (og.Nx - og.nu_hi - 1)) / og.S;
+        C acc{};
+        for (int64_t k = 0; k < og.K; ++k) {
+            int64_t beta = (top - k) % og.Nb;
+            if (beta < 0) beta += og.Nb;
+            int64_t delta = (n - beta * og.S) % og.N;
+            if (delta < 0) delta += og.N;
+            int64_t nu;
+            if (delta <= og.nu_hi) nu = delta;
+            else if (delta >= og.N - (og.Nx - og.nu_hi - 1)) nu = delta - og.N + og.Nx;
+            else continue;
+            const C v = cx[((b * og.Nb + beta) * og.Nx + nu) * og.M + m];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        c[e] = acc;
+    }
+}
+
+template <typename C>
+__global__ void ola_gather_kernel(const C* __restrict__ c, C* __restrict__ cx, OlaGeom og, int64_t B) {
+    const int64_t total = B * og.Nb * og.Nx * og.M;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = e % og.M, r = e / og.M;
+        const int64_t nu = r % og.Nx, bb = r / og.Nx;
+        const int64_t beta = bb % og.Nb, b = bb / og.Nb;
+        int64_t n = (beta * og.S + (nu <= og.nu_hi ? nu : nu - og.Nx)) % og.N;
+        if (n < 0) n += og.N;
+        cx[e] = c[(b * og.N + n) * og.M + m];
+    }
+}
+
+static unsigned ola_blocks(int64_t total) { return (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32); }
+
+template <typename T>
+cudaError_t launch_ola_split(const void* f, int f_real, void* x, const OlaGeom& og, int64_t B, cudaStream_t st) {
+    const int64_t total = B * og.Nb * og.Lx;
+    if (f_real) ola_split_kernel<T><<<ola_blocks(total), 256, 0, st>>>((const T*)f, (T*)x, og, B);
+    else ola_split_kernel<cplx<T>><<<ola_blocks(total), 256, 0, st>>>((const cplx<T>*)f, (cplx<T>*)x, og, B);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_ola_take(const void* y, int f_real, void* f, const OlaGeom& og, int64_t B, cudaStream_t st) {
+    const int64_t total = B * og.Nb * og.Lb;
+    if (f_real) ola_take_kernel<T><<<ola_blocks(total), 256, 0, st>>>((const T*)y, (T*)f, og, B);
+    else ola_take_kernel<cplx<T>><<<ola_blocks(total), 256, 0, st>>>((const cplx<T>*)y, (cplx<T>*)f, og, B);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_ola_add(const cplx<T>* cx, cplx<T>* c, const OlaGeom& og, int64_t B, cudaStream_t st) {
+    ola_add_kernel<cplx<T>><<<ola_blocks(B * og.N * og.M), 256, 0, st>>>(cx, c, og, B);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_ola_gather(const cplx<T>* c, cplx<T>* cx, const OlaGeom& og, int64_t B, cudaStream_t st) {
+    ola_gather_kernel<cplx<T>><<<ola_blocks(B * og.Nb * og.Nx * og.M), 256, 0, st>>>(c, cx, og, B);
+    return cudaGetLastError();
+}
+#define DGT_INST_OLA(T)                                                                                         \
+    template cudaError_t launch_ola_split<T>(const void*, int, void*, const OlaGeom&, int64_t, cudaStream_t);   \
+    template cudaError_t launch_ola_take<T>(const void*, int, void*, const OlaGeom&, int64_t, cudaStream_t);    \
+    template cudaError_t launch_ola_add<T>(const cplx<T>*, cplx<T>*, const OlaGeom&, int64_t, cudaStream_t);   \
+    template cudaError_t launch_ola_gather<T>(const cplx<T>*, cplx<T>*, const OlaGeom&, int64_t, cudaStream_t);
+DGT_INST_OLA(float)
+DGT_INST_OLA(double)
+
+// =====================================================================================
 // Scratch of the allocation-free FIR synthesis entry point: one fixed array per GPU that
 // loads the library, held until the process exits.  Host code must not use the symbol as
 // a pointer: its device address comes from cudaGetSymbolAddress, looked up once per device.

@@ -287,6 +287,7 @@ struct PlanCore {
     bool fir_synth_ok = true;
     std::vector<double> g_host;        // window as given (complex interleaved, float64)
     SepGeom coset_sep{};               // (lam2 a, M): used by the dual / tight Gram blocks
+    int64_t ola_block = 0, ola_len = 0;  // blockwise plans: block length and local length
 };
 
 struct dgt_plan_s {
@@ -841,7 +842,7 @@ static bool fft_ok(int64_t n, int precision) {
 static bool fft_rows_ok(int64_t n, int precision) { return fft_ok(n, precision) || row_only_len_ok(n, precision); }
 
 static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t lam1, int64_t lam2, const dgt_window* g,
-                       int route, int precision, cudaStream_t st) {
+                       int route, int precision, cudaStream_t st, bool allow_fir = true) {
     if (!out || !g || !g->data) return fail(DGT_ERR_ARG, "null plan or window pointer");
     *out = nullptr;
     if (L <= 0 || a <= 0 || M <= 0 || lam2 <= 0) return fail(DGT_ERR_ARG, "L, a, M, lambda2 must be positive");
@@ -909,7 +910,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
         }
     }
     if (route == DGT_ROUTE_AUTO) {
-        if (g->kind == DGT_WINDOW_FIR && fir_cols && fir_synth_ok && lam2 <= 8) route = DGT_ROUTE_FIR;
+        if (allow_fir && g->kind == DGT_WINDOW_FIR && fir_cols && fir_synth_ok && lam2 <= 8) route = DGT_ROUTE_FIR;
         else route = k.freq_shear ? DGT_ROUTE_COSET : DGT_ROUTE_SHEAR;
     }
     if (route == DGT_ROUTE_FIR && g->kind != DGT_WINDOW_FIR)
@@ -994,6 +995,151 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
 }
 
 // ---------------------------------------------------------------------------------------
+// Blockwise (overlap-add) plan (Section 3, OLA; Section 4, shear-OLA): blocks of Lb samples,
+// zero-extended to Lx, transformed by a full-window plan of length Lx, their coefficient
+// columns added into the long transform's columns (and the adjoint for synthesis).
+// ---------------------------------------------------------------------------------------
+template <typename T> struct OlaPlan final : dgt_plan_s {
+    using C = cplx<T>;
+    std::unique_ptr<PlanImpl<T>> inner;
+    OlaGeom og{};
+    int64_t Lg = 0, center = 0;        // the FIR window (the blocks' plan holds it expanded to Lx)
+    DevBuf work;
+
+    struct Layout { size_t x, cx, in, total; };
+    static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+    Layout layout(int64_t B) const {
+        Layout ly{};
+        ly.x = 0;
+        ly.cx = al(sizeof(C) * (size_t)B * og.Nb * og.Lx);
+        ly.in = ly.cx + al(sizeof(C) * (size_t)B * og.Nb * og.Nx * og.M);
+        ly.total = ly.in + inner->ws_bytes(B * og.Nb);
+        return ly;
+    }
+    char* workspace(int64_t B, void* wsp) {
+        if (wsp) return (char*)wsp;
+        if (work.alloc(layout(B).total) != DGT_OK) return nullptr;
+        return (char*)work.p;
+    }
+    int exec(const void* f, int f_real, void* c, int64_t B, void* wsp, cudaStream_t st) override {
+        if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+        const Layout ly = layout(B);
+        char* ws = workspace(B, wsp);
+        if (!ws) return DGT_ERR_OOM;
+        KTRY("ola_split", st, launch_ola_split<T>(f, f_real, ws + ly.x, og, B, st));
+        DGT_TRY(inner->exec(ws + ly.x, f_real, ws + ly.cx, B * og.Nb, ws + ly.in, st));
+        KTRY("ola_add", st, launch_ola_add<T>((const C*)(ws + ly.cx), (C*)c, og, B, st));
+        return DGT_OK;
+    }
+    int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, cudaStream_t st) override {
+        if (which < 0 || which > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which);
+        if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+        if (which) {
+            if (wsp && !inner->zg_ok[which])
+                return fail(DGT_ERR_ARG, "the dual / tight window is not cached yet (call dgt_window_dual/_tight)");
+            DGT_TRY(inner->ensure_window(which, st));
+        }
+        const Layout ly = layout(B);
+        char* ws = workspace(B, wsp);
+        if (!ws) return DGT_ERR_OOM;
+        KTRY("ola_gather", st, launch_ola_gather<T>((const C*)c, (C*)(ws + ly.cx), og, B, st));
+        DGT_TRY(inner->iexec(ws + ly.cx, ws + ly.x, f_real, B * og.Nb, which, ws + ly.in, st));
+        KTRY("ola_take", st, launch_ola_take<T>(ws + ly.x, f_real, f, og, B, st));
+        return DGT_OK;
+    }
+    // the window on Z_L: the local window's taps moved from Z_Lx to Z_L (the dual of a window
+    // no longer than M is the same on both: S is diagonal with the same a-periodic weights)
+    int window_out(int which, void* out, cudaStream_t st) override {
+        const PlanCore& k = core;
+        DevBuf loc;
+        DGT_TRY(loc.alloc(sizeof(C) * (size_t)og.Lx));
+        DGT_TRY(inner->window_out(which, loc.p, st));
+        std::vector<T> lw(2 * og.Lx), gw(2 * k.L, (T)0);
+        CUDA_TRY(cudaMemcpyAsync(lw.data(), loc.p, sizeof(C) * og.Lx, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t t = 0; t < Lg; ++t) {
+            const int64_t li = pmod(t - center, og.Lx), gi = pmod(t - center, k.L);
+            gw[2 * gi] = lw[2 * li];
+            gw[2 * gi + 1] = lw[2 * li + 1];
+        }
+        CUDA_TRY(cudaMemcpyAsync(out, gw.data(), sizeof(C) * k.L, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return DGT_OK;
+    }
+    int set_window(const void*, int, cudaStream_t) override {
+        return fail(DGT_ERR_UNSUPPORTED, "blockwise plans keep the window they were created with");
+    }
+    int grad_window(const void*, int, const void*, void*, int, int64_t, cudaStream_t) override {
+        return fail(DGT_ERR_UNSUPPORTED, "window gradient needs a full-length window");
+    }
+    int logmag(const void*, void*, double*, double, int64_t, cudaStream_t) override {
+        return fail(DGT_ERR_UNSUPPORTED, "use a plain plan of the same lattice for the loss helper");
+    }
+    int fir_synthesis_noalloc(const void*, void*, int, int64_t, int, cudaStream_t) override {
+        return fail(DGT_ERR_ARG, "allocation-free synthesis needs an FIR-route plan");
+    }
+    int status_check(cudaStream_t st) override { return inner->status_check(st); }
+    size_t ws_bytes(int64_t B) const override { return layout(B).total; }
+    size_t owned_bytes() const override { return inner->owned_bytes() + work.bytes; }
+};
+
+static int create_ola_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t lam1, int64_t lam2,
+                           const dgt_window* g, int64_t Lb, int inner_route, int precision, cudaStream_t st) {
+    if (!out || !g || !g->data) return fail(DGT_ERR_ARG, "null plan or window pointer");
+    *out = nullptr;
+    if (g->kind != DGT_WINDOW_FIR) return fail(DGT_ERR_ARG, "blockwise plans need an FIR window");
+    if (inner_route != DGT_ROUTE_AUTO && inner_route != DGT_ROUTE_COSET && inner_route != DGT_ROUTE_SHEAR)
+        return fail(DGT_ERR_ARG, "blockwise plans run the coset or the shear route on the blocks");
+    if (L <= 0 || a <= 0 || M <= 0 || lam2 <= 0 || Lb <= 0) return fail(DGT_ERR_ARG, "sizes must be positive");
+    if (lam1 < 0 || lam1 >= lam2 || igcd(lam1, lam2) != 1) return fail(DGT_ERR_ARG, "need 0 <= lambda1 < lambda2, gcd 1");
+    const int64_t q = lam2 * ilcm(a, M);
+    if (L % q) return fail(DGT_ERR_LENGTH, "L=%lld is not a multiple of lambda2*lcm(a,M)=%lld", (long long)L, (long long)q);
+    if (L % Lb || Lb % q)
+        return fail(DGT_ERR_LENGTH, "block length %lld must divide L and be a multiple of lambda2*lcm(a,M)=%lld",
+                    (long long)Lb, (long long)q);
+    if (g->len <= 0 || g->center < 0 || g->center >= g->len) return fail(DGT_ERR_ARG, "bad FIR window");
+    if (Lb < g->len) return fail(DGT_ERR_ARG, "the block must be at least as long as the window");
+    // the smallest admissible length Lx >= Lb + Lg whose transform this build supports (FFT
+    // lengths with prime factors up to 7, tiles that fit)
+    int64_t Lx = (Lb + g->len + q - 1) / q * q;
+    if (Lx > L) return fail(DGT_ERR_LENGTH, "the extended block (%lld) is longer than the signal", (long long)Lx);
+    dgt_plan_t in = nullptr;
+    for (int tries = 0;; ++tries, Lx += q) {
+        if (Lx > L || tries == 64)
+            return fail(DGT_ERR_UNSUPPORTED, "no supported block transform length from %lld", (long long)(Lb + g->len));
+        const int s = create_plan(&in, Lx, a, M, lam1, lam2, g, inner_route, precision, st, /*allow_fir=*/false);
+        if (s == DGT_OK) break;
+        if (s != DGT_ERR_UNSUPPORTED) return s;
+    }
+    OlaGeom og{};
+    og.L = L; og.a = a; og.M = M; og.N = L / a; og.Lb = Lb; og.Nb = L / Lb; og.Lx = Lx; og.Nx = Lx / a;
+    og.S = Lb / a; og.nu_hi = (Lb - 1 + g->center) / a;
+    og.K = std::min<int64_t>(og.Nb, (og.Nx + og.S - 1) / og.S + 1);
+    PlanCore k = in->core;
+    k.L = L; k.N = L / a; k.b = L / M; k.s = k.b * lam1 / lam2;
+    k.ola_block = Lb;
+    k.ola_len = Lx;
+    if (precision == DGT_F32) {
+        auto* p = new OlaPlan<float>();
+        p->inner.reset(static_cast<PlanImpl<float>*>(in));
+        p->og = og;
+        p->Lg = g->len;
+        p->center = g->center;
+        p->core = k;
+        *out = p;
+    } else {
+        auto* p = new OlaPlan<double>();
+        p->inner.reset(static_cast<PlanImpl<double>*>(in));
+        p->og = og;
+        p->Lg = g->len;
+        p->center = g->center;
+        p->core = k;
+        *out = p;
+    }
+    return DGT_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // extern "C"
 // ---------------------------------------------------------------------------------------
 extern "C" {
@@ -1002,6 +1148,16 @@ int dgt_plan_create(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t l
                     const dgt_window* g, int route, int precision, void* stream) {
     try {
         return create_plan(plan, L, a, M, lambda1, lambda2, g, route, precision, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        return fail(DGT_ERR_OOM, "host allocation failed");
+    }
+}
+
+int dgt_plan_create_ola(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t lambda1, int64_t lambda2,
+                        const dgt_window* g, int64_t block_len, int inner_route, int precision, void* stream) {
+    try {
+        return create_ola_plan(plan, L, a, M, lambda1, lambda2, g, block_len, inner_route, precision,
+                               (cudaStream_t)stream);
     } catch (const std::bad_alloc&) {
         return fail(DGT_ERR_OOM, "host allocation failed");
     }
@@ -1020,6 +1176,8 @@ int dgt_plan_get_info(dgt_plan_t plan, dgt_plan_info* info) {
     info->c = k.sep.c; info->d = k.sep.d; info->p = k.sep.p; info->q = k.sep.q;
     info->n_windows = k.J;
     info->fir_len = k.route == DGT_ROUTE_FIR ? k.Lg : 0;
+    info->ola_block = k.ola_block;
+    info->ola_len = k.ola_len;
     return DGT_OK;
 }
 
