@@ -470,6 +470,44 @@ def run_other_configs(dev, steps=5):
     p.close()
     del f, gw
     torch.cuda.empty_cache()
+    # blockwise (overlap-add) plans on the audio batch, Hann window of 1024 taps: blocks of
+    # 2^14 and 2^16 samples through the coset and the shear route, against the FIR route
+    from workloads import AUDIO_BATCH, hann_taps
+
+    w = AUDIO_BATCH
+    Bo = 16
+    f = torch.from_numpy(signal_batch(w, count=Bo, cfg_id=1).astype(np.float32)).to(dev)
+    taps, center = hann_taps(1024)
+    taps = taps / np.linalg.norm(taps)
+    c = torch.empty((Bo, w.N, w.M), dtype=torch.complex64, device=dev)
+    fr = torch.empty_like(f)
+    ola = {"workload": w.name, "batch": Bo, "window": "hann1024", "step": "analysis + dual synthesis"}
+    for name, kw in (("fir_route", {"route": "fir"}),
+                     ("ola_b16384_coset", {"route": "coset", "block_len": 1 << 14}),
+                     ("ola_b16384_shear", {"route": "shear", "block_len": 1 << 14}),
+                     ("ola_b65536_coset", {"route": "coset", "block_len": 1 << 16})):
+        try:
+            p = Plan(w.L, w.a, w.M, w.lam1, w.lam2, taps, precision="f32", fir_center=center, **kw)
+        except Exception as e:                    # an unsupported block length: say so
+            ola[name] = {"unsupported": str(e)[:120]}
+            continue
+        p.dual_window()
+
+        def step():
+            p.dgt(f, out=c)
+            p.idgt(c, window="dual", real=True, out=fr)
+
+        ms = _time_cuda(step, steps)
+        ent = {"ms_per_step": ms, "coef_per_s": 2 * Bo * w.M * w.N / (ms * 1e-3),
+               "reconstruction_rel_err": float(torch.linalg.vector_norm(fr - f) / torch.linalg.vector_norm(f))}
+        if "block_len" in kw:
+            ent["block_transform_len"] = p.info["ola_len"]
+            ent["rho"] = p.info["ola_len"] / kw["block_len"]
+        ola[name] = ent
+        p.close()
+    out["blockwise"] = ola
+    del f, c, fr
+    torch.cuda.empty_cache()
     # small float64 lattice: one signal, analysis + dual synthesis, both routes (latency)
     w = QUINCUNX_FP64
     f = torch.from_numpy(complex_normal(w.L, 1, 0)).to(dev)[None]
