@@ -558,6 +558,45 @@ def run_serve(seconds, rate=2000.0, cap_bytes=40 << 30, seed=4, infeasible_every
     return out
 
 
+def run_lambda_sweep(dev, steps=5, batch=8):
+    """The experiment of Fig. 2 on the GPU: time of the coset and the shear route of one
+    analysis as lambda2 goes from 1 to 10 (lambda1 = 1), for (a, M) in {(32, 64), (40, 60),
+    (60, 80)} and L = lcm(a, M) * 2520 (admissible for every lambda2 <= 10), float32,
+    `batch` complex N(0,1) signals, periodised Gaussian window."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_1307_4569_gb300 import Plan
+    from workloads import complex_normal, gaussian_window
+
+    rows = []
+    for a, M in ((32, 64), (40, 60), (60, 80)):
+        L = a * M // math.gcd(a, M) * 2520
+        f = torch.from_numpy(np.stack([complex_normal(L, 77, i) for i in range(batch)]).astype(np.complex64)).to(dev)
+        g = gaussian_window(L)
+        c = torch.empty((batch, L // a, M), dtype=torch.complex64, device=dev)
+        for lam2 in range(1, 11):
+            lam1 = 0 if lam2 == 1 else 1
+            ent = {"a": a, "M": M, "L": L, "lambda2": lam2}
+            for route in ("coset", "shear"):
+                try:
+                    p = Plan(L, a, M, lam1, lam2, g, route=route, precision="f32")
+                except Exception as e:
+                    ent[route] = {"unsupported": str(e)[:100]}
+                    continue
+                ms = _time_cuda(lambda: p.dgt(f, out=c), steps)
+                ent[route] = {"ms": ms, "coef_per_s": batch * M * (L // a) / (ms * 1e-3), "s0": p.info["s0"]}
+                p.close()
+            if "ms" in ent.get("coset", {}) and "ms" in ent.get("shear", {}):
+                ent["shear_over_coset"] = ent["shear"]["ms"] / ent["coset"]["ms"]
+            rows.append(ent)
+        del f, c
+        torch.cuda.empty_cache()
+    return rows
+
+
 def make_plan_names():
     return [("hann-fir", None), ("gauss-shear", None), ("gauss-coset", None)]
 
@@ -651,11 +690,22 @@ def main():
     ap.add_argument("--cpu-procs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0, help="signals per step (default: the workload's 64)")
     ap.add_argument("--other-configs", type=int, default=1, help="1: also time the other workloads briefly")
+    ap.add_argument("--lambda-sweep", action="store_true",
+                    help="run only the coset / shear timing sweep over lambda2 = 1..10 (Fig. 2 setups) and "
+                         "print its rows as one JSON line")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the serving run (Poisson 2000 requests/s); 0 skips it")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.lambda_sweep:
+        import torch
+
+        from paper_1307_4569_gb300 import build as bld
+
+        bld.build()
+        print(json.dumps({"lambda_sweep": run_lambda_sweep(torch.device("cuda", 0))}), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
         if line is not None:
