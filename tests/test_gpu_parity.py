@@ -264,3 +264,42 @@ def test_errors_and_edges():
     c2 = torch.empty_like(c1)
     p.dgt_ws(f, c2, ws)
     assert torch.equal(c1, c2)
+
+
+# -------------------------------------------------------------------------------------
+# degenerate lattices: one channel, one sample per time step, critical sampling, a = M,
+# a single column per coset, and the empty batch on every entry point
+# -------------------------------------------------------------------------------------
+DEGENERATE = [
+    (16, 2, 1, 0, 1),       # M = 1: one frequency channel
+    (64, 1, 4, 1, 2),       # a = 1: every time shift
+    (96, 8, 8, 1, 2),       # a = M: critical sampling (redundancy 1)
+    (64, 4, 64, 0, 1),      # M = L: one time-frequency tile per time step, b = 1
+    (72, 6, 12, 1, 3),      # N = 12 columns, lambda2 = 3: four columns per coset
+]
+
+
+@pytest.mark.parametrize("params", DEGENERATE)
+def test_degenerate_lattices(params):
+    Plan = _P()
+    L, a, M, l1, l2 = params
+    assert OL.feasible(L, a, M, l1, l2)
+    rng = np.random.default_rng(L + 13 * M + a)
+    g = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    f = rng.standard_normal((2, L)) + 1j * rng.standard_normal((2, L))
+    for route in ("coset", "shear"):
+        p = Plan(L, a, M, l1, l2, g, route=route, precision="f64")
+        c = p.dgt(_to_dev(f, "f64")).cpu().numpy()
+        for b in range(2):
+            ref = OD.dgt_direct(f[b], g, a, M, l1, l2).T
+            assert _rel(c[b], ref) <= 1e-12, (route, b, p.info)
+        cc = rng.standard_normal((2, L // a, M)) + 1j * rng.standard_normal((2, L // a, M))
+        fs = p.idgt(_to_dev(cc, "f64"), window="adjoint").cpu().numpy()
+        for b in range(2):
+            assert _rel(fs[b], OD.idgt_direct(cc[b].T, g, a, M, l1, l2)) <= 1e-12, (route, "synthesis")
+        # empty batches on every entry point
+        e = torch.empty((0, L), dtype=torch.complex128, device="cuda")
+        assert p.dgt(e).shape == (0, L // a, M)
+        ec = torch.empty((0, L // a, M), dtype=torch.complex128, device="cuda")
+        assert p.idgt(ec, window="adjoint").shape == (0, L)
+        p.close()
