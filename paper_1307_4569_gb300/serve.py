@@ -259,6 +259,7 @@ class GpuExecutor:
         self.keep = keep_results
         self.results = {}
         self.plans = {}
+        self.windows = {}
         self.inputs = {}
         self.rings = {}
 
@@ -271,6 +272,12 @@ class GpuExecutor:
         from .api import Plan
 
         L, a, M, lam1, lam2, window = key
+        # an inadmissible lattice is refused before its window is built (building a
+        # 2^20-sample window takes tens of milliseconds, a stall for every queued request);
+        # the library applies the same rule (Prop. minsig) and would return DGT_ERR_LENGTH
+        q = lam2 * (a * M // math.gcd(a, M))
+        if L % q:
+            raise DGTError(2, "L=%d is not a multiple of lambda2*lcm(a,M)=%d" % (L, q))
         with self.torch.cuda.stream(self.stream):
             if window.startswith("hann"):
                 taps, center = hann_taps(int(window[4:]))
@@ -278,7 +285,9 @@ class GpuExecutor:
                 p = Plan(L, a, M, lam1, lam2, taps, route="auto", precision=self.precision, fir_center=center,
                          stream=self.stream)
             else:
-                p = Plan(L, a, M, lam1, lam2, gaussian_window(L), route="auto", precision=self.precision,
+                if L not in self.windows:
+                    self.windows[L] = gaussian_window(L)
+                p = Plan(L, a, M, lam1, lam2, self.windows[L], route="auto", precision=self.precision,
                          stream=self.stream)
             p.dual_window(stream=self.stream)          # plan-time set-up of the synthesis window
         self.plans[key] = p
