@@ -690,6 +690,9 @@ def main():
     ap.add_argument("--cpu-procs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0, help="signals per step (default: the workload's 64)")
     ap.add_argument("--other-configs", type=int, default=1, help="1: also time the other workloads briefly")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="run only the serving loop at rising request rates and under a 256 MB admission cap, "
+                         "and print its rows as one JSON line")
     ap.add_argument("--lambda-sweep", action="store_true",
                     help="run only the coset / shear timing sweep over lambda2 = 1..10 (Fig. 2 setups) and "
                          "print its rows as one JSON line")
@@ -698,6 +701,21 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.serve_sweep:
+        from paper_1307_4569_gb300 import build as bld
+
+        bld.build()
+        rows = []
+        for rate in (2000, 4000, 8000, 16000, 32000):
+            r = run_serve(5.0, rate=rate)
+            rows.append({k: r[k] for k in ("rate_per_s", "requests", "ok", "p50_ms", "p99_ms", "max_ms",
+                                            "queue_wait_p99_ms", "mean_batch", "coef_per_s", "host_busy_frac")})
+        r = run_serve(5.0, rate=2000, cap_bytes=256 << 20)
+        rows.append({"cap_bytes": 256 << 20, **{k: r[k] for k in ("rate_per_s", "requests", "ok", "rejected", "p50_ms",
+                                                                   "p99_ms", "max_ms", "peak_inflight_bytes",
+                                                                   "mean_batch")}})
+        print(json.dumps({"serve_sweep": rows}), flush=True)
+        return
     if args.lambda_sweep:
         import torch
 

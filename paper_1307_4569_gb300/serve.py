@@ -409,7 +409,11 @@ class GpuExecutor:
             except DGTError:
                 continue
             for kind in kinds:
-                self.finish(self.launch(key, kind, [None] * batch, list(range(batch))))
+                n = batch
+                while n > 0 and self.max_batch_bytes is not None and self.bytes_for(key, kind, n) > self.max_batch_bytes:
+                    n -= 1
+                if n:                            # a request that fits no arena is rejected when served
+                    self.finish(self.launch(key, kind, [None] * n, list(range(n))))
         self.results.clear()
         self.torch.cuda.synchronize(self.dev)
 
