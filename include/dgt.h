@@ -137,6 +137,18 @@ int dgt_exec(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t bat
 int idgt_exec(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
               void* stream);
 
+/* Real-signal coefficients (the real-signal variant of the interface, Section 5): for a real
+ * signal and a real window on a lattice with lambda2 <= 2 and M even,
+ * c(m, n) = conj(c((-m - 2 w(n)) mod M, n)), so the channels 0..M/2 determine c.
+ * dgt_exec_real: f DEVICE [batch][L] real -> c DEVICE [batch][N][M/2 + 1] complex.
+ * idgt_exec_real: the synthesis of the full coefficients those channels stand for, real
+ * output [batch][L]; which_window as for idgt_exec.  Both stage the full array in
+ * plan-owned memory (one call at a time per plan).
+ * Errors: DGT_ERR_UNSUPPORTED (lambda2 > 2, odd M, complex window), and those of
+ * dgt_exec / idgt_exec. */
+int dgt_exec_real(dgt_plan_t plan, const void* f, void* c, int64_t batch, void* stream);
+int idgt_exec_real(dgt_plan_t plan, const void* c, void* f, int64_t batch, int which_window, void* stream);
+
 /* Workspace needed by dgt_exec_ws / idgt_exec_ws for `batch` signals, in bytes. */
 int dgt_workspace_bytes(dgt_plan_t plan, int64_t batch, size_t* bytes);
 

@@ -51,6 +51,8 @@ SIGNATURES = {
     "dgt_plan_get_info": (i32, [vp, C.POINTER(PlanInfo)]),
     "dgt_plan_set_window": (i32, [vp, vp, i32, vp]),
     "dgt_exec": (i32, [vp, vp, i32, vp, i64, vp]),
+    "dgt_exec_real": (i32, [vp, vp, vp, i64, vp]),
+    "idgt_exec_real": (i32, [vp, vp, vp, i64, i32, vp]),
     "idgt_exec": (i32, [vp, vp, vp, i32, i64, i32, vp]),
     "dgt_workspace_bytes": (i32, [vp, i64, C.POINTER(C.c_size_t)]),
     "dgt_exec_ws": (i32, [vp, vp, i32, vp, i64, vp, vp]),

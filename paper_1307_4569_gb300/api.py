@@ -113,6 +113,30 @@ class Plan:
                                   _stream(stream)))
         return out
 
+    def dgtreal(self, f: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Channels 0..M/2 of the coefficients of real signals f[..., L] (real window,
+        lambda2 <= 2, M even): c[..., n, m], m <= M/2."""
+        self._check_signal(f)
+        if f.is_complex():
+            raise TypeError("dgtreal needs real signals")
+        B = int(np.prod(f.shape[:-1])) if f.dim() > 1 else 1
+        if out is None:
+            out = torch.empty(tuple(f.shape[:-1]) + (self.N, self.M // 2 + 1), dtype=self.cdtype, device=f.device)
+        K.check(K.lib().dgt_exec_real(self._h, f.data_ptr(), out.data_ptr(), B, _stream(stream)))
+        return out
+
+    def idgtreal(self, c: torch.Tensor, window: str = "dual", out=None, stream=None) -> torch.Tensor:
+        """Real synthesis from channels 0..M/2 (the inverse of dgtreal with the dual window)."""
+        if not c.is_cuda or not c.is_contiguous() or c.dtype != self.cdtype:
+            raise TypeError("coefficients must be a contiguous CUDA %s tensor" % self.cdtype)
+        if tuple(c.shape[-2:]) != (self.N, self.M // 2 + 1):
+            raise ValueError("coefficient shape %s != (N, M/2+1)" % (tuple(c.shape),))
+        B = int(np.prod(c.shape[:-2])) if c.dim() > 2 else 1
+        if out is None:
+            out = torch.empty(tuple(c.shape[:-2]) + (self.L,), dtype=self.rdtype, device=c.device)
+        K.check(K.lib().idgt_exec_real(self._h, c.data_ptr(), out.data_ptr(), B, _SYN[window], _stream(stream)))
+        return out
+
     def dual_window(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.L, dtype=self.cdtype, device="cuda")
         K.check(K.lib().dgt_window_dual(self._h, out.data_ptr(), _stream(stream)))

@@ -149,6 +149,13 @@ cudaError_t launch_ola_add(const cplx<T>* cx, cplx<T>* c, const OlaGeom& og, int
 template <typename T>
 cudaError_t launch_ola_gather(const cplx<T>* c, cplx<T>* cx, const OlaGeom& og, int64_t B, cudaStream_t st);
 
+// real-signal coefficients: channels 0..M/2 (compact) and the full array back (expand)
+template <typename T>
+cudaError_t launch_half_compact(const cplx<T>* full, cplx<T>* half, int64_t N, int64_t M, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t launch_half_expand(const cplx<T>* half, cplx<T>* full, int64_t N, int64_t M, int64_t lam1, int64_t lam2,
+                               int64_t B, cudaStream_t st);
+
 // elementwise helpers
 template <typename T>
 cudaError_t launch_coset_windows(const cplx<T>* g, cplx<T>* gj, int64_t L, int64_t a, int64_t J, const int64_t* sigma,

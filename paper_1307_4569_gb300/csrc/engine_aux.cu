@@ -640,6 +640,64 @@ DGT_INST_OLA(float)
 DGT_INST_OLA(double)
 
 // =====================================================================================
+// Real-signal coefficients: channels 0..M/2 of every column (Mh = M/2 + 1), and the full
+// array back from them by conj(c(m, n)) = c((-m - 2 w(n)) mod M, n), 2 w(n) = (n lam1) mod lam2
+// for lam2 <= 2.
+// =====================================================================================
+template <typename C>
+__global__ void half_compact_kernel(const C* __restrict__ full, C* __restrict__ half, int64_t N, int64_t M,
+                                    int64_t B) {
+    const int64_t Mh = M / 2 + 1;
+    const int64_t total = B * N * Mh;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = e % Mh, r = e / Mh;
+        half[e] = full[r * M + m];
+    }
+}
+
+template <typename C>
+__global__ void half_expand_kernel(const C* __restrict__ half, C* __restrict__ full, int64_t N, int64_t M,
+                                   int64_t lam1, int64_t lam2, int64_t B) {
+    const int64_t Mh = M / 2 + 1;
+    const int64_t total = B * N * M;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = e % M, r = e / M;
+        if (m < Mh) {
+            full[e] = half[r * Mh + m];
+        } else {
+            const int64_t n = r % N;
+            const int64_t two_w = ((n * lam1) % lam2) * (2 / lam2);
+            int64_t pm = (-m - two_w) % M;
+            if (pm < 0) pm += M;
+            C v = half[r * Mh + pm];
+            v.y = -v.y;
+            full[e] = v;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_half_compact(const cplx<T>* full, cplx<T>* half, int64_t N, int64_t M, int64_t B, cudaStream_t st) {
+    const int64_t total = B * N * (M / 2 + 1);
+    half_compact_kernel<cplx<T>><<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, st>>>(full, half, N, M, B);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_half_expand(const cplx<T>* half, cplx<T>* full, int64_t N, int64_t M, int64_t lam1, int64_t lam2,
+                               int64_t B, cudaStream_t st) {
+    const int64_t total = B * N * M;
+    half_expand_kernel<cplx<T>><<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32), 256, 0, st>>>(
+        half, full, N, M, lam1, lam2, B);
+    return cudaGetLastError();
+}
+template cudaError_t launch_half_compact<float>(const float2*, float2*, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_half_compact<double>(const double2*, double2*, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_half_expand<float>(const float2*, float2*, int64_t, int64_t, int64_t, int64_t, int64_t,
+                                               cudaStream_t);
+template cudaError_t launch_half_expand<double>(const double2*, double2*, int64_t, int64_t, int64_t, int64_t, int64_t,
+                                                cudaStream_t);
+
+// =====================================================================================
 // Scratch of the allocation-free FIR synthesis entry point: one fixed array per GPU that
 // loads the library, held until the process exits.  Host code must not use the symbol as
 // a pointer: its device address comes from cudaGetSymbolAddress, looked up once per device.

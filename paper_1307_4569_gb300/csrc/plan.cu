@@ -304,7 +304,37 @@ struct dgt_plan_s {
     virtual int status_check(cudaStream_t st) = 0;
     virtual size_t ws_bytes(int64_t B) const = 0;
     virtual size_t owned_bytes() const = 0;
+    // real-signal analysis / synthesis on channels 0..M/2 (through a plan-owned full array)
+    virtual int exec_real(const void* f, void* ch, int64_t B, cudaStream_t st) = 0;
+    virtual int iexec_real(const void* ch, void* f, int64_t B, int which, cudaStream_t st) = 0;
+    DevBuf real_full;                  // staging for the real-signal entry points
 };
+
+// the real-signal symmetry holds for a real window, lambda2 <= 2 and an even M
+static int real_ok(const PlanCore& k) {
+    if (k.lam2 > 2 || k.M % 2) return fail(DGT_ERR_UNSUPPORTED, "real-signal coefficients need lambda2 <= 2 and an even M");
+    if (!k.win_real) return fail(DGT_ERR_UNSUPPORTED, "real-signal coefficients need a real window");
+    return DGT_OK;
+}
+template <typename T> static int exec_real_via(dgt_plan_s* p, const void* f, void* ch, int64_t B, cudaStream_t st) {
+    const PlanCore& k = p->core;
+    DGT_TRY(real_ok(k));
+    if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+    DGT_TRY(p->real_full.alloc(sizeof(cplx<T>) * (size_t)B * k.N * k.M));
+    DGT_TRY(p->exec(f, 1, p->real_full.p, B, nullptr, st));
+    KTRY("half_compact", st, launch_half_compact<T>((const cplx<T>*)p->real_full.p, (cplx<T>*)ch, k.N, k.M, B, st));
+    return DGT_OK;
+}
+template <typename T>
+static int iexec_real_via(dgt_plan_s* p, const void* ch, void* f, int64_t B, int which, cudaStream_t st) {
+    const PlanCore& k = p->core;
+    DGT_TRY(real_ok(k));
+    if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+    DGT_TRY(p->real_full.alloc(sizeof(cplx<T>) * (size_t)B * k.N * k.M));
+    KTRY("half_expand", st, launch_half_expand<T>((const cplx<T>*)ch, (cplx<T>*)p->real_full.p, k.N, k.M, k.lam1, k.lam2,
+                                                  B, st));
+    return p->iexec(p->real_full.p, f, 1, B, which, nullptr, st);
+}
 
 template <typename T> struct PlanImpl final : dgt_plan_s {
     using C = cplx<T>;
@@ -374,7 +404,8 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     }
     size_t ws_bytes(int64_t B) const override { return layout(B).total; }
     size_t owned_bytes() const override {
-        size_t s = sigma.bytes + g64.bytes + gT.bytes + work.bytes + tmpwin.bytes + status.bytes + lossparts.bytes;
+        size_t s = sigma.bytes + g64.bytes + gT.bytes + work.bytes + tmpwin.bytes + status.bytes + lossparts.bytes +
+                   real_full.bytes;
         for (int i = 0; i < 3; ++i) s += zg[i].bytes + gam[i].bytes + firmt[i].bytes;
         for (auto& kv : tw) s += kv.second->buf.bytes;
         s += cisL.hi.bytes + cisL.lo.bytes + cis2L.hi.bytes + cis2L.lo.bytes + cis2N.hi.bytes + cis2N.lo.bytes +
@@ -524,6 +555,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         const int64_t n = k.win_kind == DGT_WINDOW_FIR ? k.Lg : k.L;
         CUDA_TRY(launch_convert<T, T>(g, is_real, (C*)gT.p, n, st));
         CUDA_TRY(launch_convert<T, double>(g, is_real, (double2*)g64.p, n, st));
+        core.win_real = is_real;
         zg_ok[1] = zg_ok[2] = false;
         return build_factor(0, (const C*)gT.p, st);
     }
@@ -779,6 +811,12 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         CUDA_TRY(cudaStreamSynchronize(st));
         CUDA_TRY(cudaGetLastError());
         return DGT_OK;
+    }
+    int exec_real(const void* f, void* ch, int64_t B, cudaStream_t st) override {
+        return exec_real_via<T>(this, f, ch, B, st);
+    }
+    int iexec_real(const void* ch, void* f, int64_t B, int which, cudaStream_t st) override {
+        return iexec_real_via<T>(this, ch, f, B, which, st);
     }
 
     // FIR synthesis whose seam scratch is the library's fixed per-GPU array: no allocation.
@@ -1079,8 +1117,14 @@ template <typename T> struct OlaPlan final : dgt_plan_s {
         return fail(DGT_ERR_ARG, "allocation-free synthesis needs an FIR-route plan");
     }
     int status_check(cudaStream_t st) override { return inner->status_check(st); }
+    int exec_real(const void* f, void* ch, int64_t B, cudaStream_t st) override {
+        return exec_real_via<T>(this, f, ch, B, st);
+    }
+    int iexec_real(const void* ch, void* f, int64_t B, int which, cudaStream_t st) override {
+        return iexec_real_via<T>(this, ch, f, B, which, st);
+    }
     size_t ws_bytes(int64_t B) const override { return layout(B).total; }
-    size_t owned_bytes() const override { return inner->owned_bytes() + work.bytes; }
+    size_t owned_bytes() const override { return inner->owned_bytes() + work.bytes + real_full.bytes; }
 };
 
 static int create_ola_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t lam1, int64_t lam2,
@@ -1194,6 +1238,17 @@ int dgt_exec(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t bat
 int idgt_exec(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window, void* stream) {
     if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
     return plan->iexec(c, f, f_real_out, batch, which_window, nullptr, (cudaStream_t)stream);
+}
+
+int dgt_exec_real(dgt_plan_t plan, const void* f, void* c, int64_t batch, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    return plan->exec_real(f, c, batch, (cudaStream_t)stream);
+}
+
+int idgt_exec_real(dgt_plan_t plan, const void* c, void* f, int64_t batch, int which_window, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    if (which_window < 0 || which_window > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which_window);
+    return plan->iexec_real(c, f, batch, which_window, (cudaStream_t)stream);
 }
 
 int dgt_workspace_bytes(dgt_plan_t plan, int64_t batch, size_t* bytes) {
