@@ -508,6 +508,32 @@ def run_other_configs(dev, steps=5):
     out["blockwise"] = ola
     del f, c, fr
     torch.cuda.empty_cache()
+    # real-signal coefficients (channels 0..M/2) on the audio batch, FIR route, 64 signals:
+    # device time and end to end with the coefficients copied to pinned host memory
+    B = w.batch
+    f = torch.from_numpy(signal_batch(w, count=B, cfg_id=1).astype(np.float32)).to(dev)
+    p = Plan(w.L, w.a, w.M, w.lam1, w.lam2, taps, route="fir", precision="f32", fir_center=center)
+    p.dual_window()
+    c = torch.empty((B, w.N, w.M), dtype=torch.complex64, device=dev)
+    ch = torch.empty((B, w.N, w.M // 2 + 1), dtype=torch.complex64, device=dev)
+    fr = torch.empty_like(f)
+    c_host = torch.empty(c.shape, dtype=c.dtype).pin_memory()
+    ch_host = torch.empty(ch.shape, dtype=ch.dtype).pin_memory()
+    real = {"workload": w.name, "batch": B, "route": "fir", "window": "hann1024",
+            "step": "analysis + dual synthesis; e2e adds the coefficients' copy to pinned host memory"}
+    full_ms = _time_cuda(lambda: (p.dgt(f, out=c), p.idgt(c, window="dual", real=True, out=fr)), steps)
+    half_ms = _time_cuda(lambda: (p.dgtreal(f, out=ch), p.idgtreal(ch, window="dual", out=fr)), steps)
+    full_e2e = _time_cuda(lambda: (p.dgt(f, out=c), c_host.copy_(c, non_blocking=True),
+                                   p.idgt(c, window="dual", real=True, out=fr)), 3, 1)
+    half_e2e = _time_cuda(lambda: (p.dgtreal(f, out=ch), ch_host.copy_(ch, non_blocking=True),
+                                   p.idgtreal(ch, window="dual", out=fr)), 3, 1)
+    real.update({"full_ms": full_ms, "real_ms": half_ms, "full_e2e_ms": full_e2e, "real_e2e_ms": half_e2e,
+                 "coefficient_bytes_full": c.numel() * 8, "coefficient_bytes_real": ch.numel() * 8,
+                 "reconstruction_rel_err": float(torch.linalg.vector_norm(fr - f) / torch.linalg.vector_norm(f))})
+    out["real_signal"] = real
+    p.close()
+    del f, c, ch, fr, c_host, ch_host
+    torch.cuda.empty_cache()
     # small float64 lattice: one signal, analysis + dual synthesis, both routes (latency)
     w = QUINCUNX_FP64
     f = torch.from_numpy(complex_normal(w.L, 1, 0)).to(dev)[None]

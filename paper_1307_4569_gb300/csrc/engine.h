@@ -46,6 +46,8 @@ template <typename C> struct PostParams {
     ModU64 mL, mN, m2N;               // reductions modulo L, N, 2N
     ModU64 mb;                        // division by b
     ModU64 mJN, mNs;                  // row = (b J + j) Ns + n of Y: division by J Ns and Ns (set by the launchers)
+    int64_t lam1;                     // w(n) of the output columns (real-signal coefficients)
+    int half;                         // coefficients hold channels 0..M/2 only (real signals, lam2 <= 2)
 };
 
 // Signal pre-processing inside the factorisation / FFT_L passes.
@@ -121,6 +123,7 @@ template <typename C> struct FirParams {
     ModU64 mN;                        // division by N (row = b N + n)
     int64_t cols;                     // time positions per CTA
     int64_t group;                    // rows transformed at once (spare buffer rows)
+    int half;                         // coefficients hold channels 0..M/2 only (real signals, lam2 <= 2)
 };
 template <typename T>
 cudaError_t launch_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp,

@@ -108,6 +108,7 @@ cudaError_t launch_fir_analysis(const void* f, int f_real, cplx<T>* c, const Fir
         const cudaError_t e = p2_fir_analysis<T>(f, f_real, c, fp, fm.tw, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
+    if (fp.half) return cudaErrorNotSupported;       // half-channel output: power-of-two kernels only
     const int64_t S = fp.a * (fp.cols - 1) + fp.Lg;
     const size_t smem = sizeof(C) * ((size_t)(fp.cols + fp.group) * (fp.M + 1) + S);
     if (smem > kSmemBudget) return cudaErrorInvalidValue;
@@ -208,6 +209,7 @@ cudaError_t launch_fir_synthesis(const cplx<T>* c, void* f, int f_real, cplx<T>*
     if (fp.a * fp.cols < fp.Lg - fp.a) return cudaErrorInvalidValue;
     const int64_t nchunks = fp.N / fp.cols;
     cudaError_t e = p2_fir_synthesis<T>(c, f, f_real, seams, fp, fm.tw, B, st);
+    if (e == cudaErrorNotSupported && fp.half) return e;  // half-channel input: power-of-two kernels only
     if (e == cudaErrorNotSupported) {
         const size_t smem = sizeof(C) * ((size_t)(fp.cols + fp.group) * (fp.M + 1));
         if (smem > kSmemBudget) return cudaErrorInvalidValue;

@@ -222,6 +222,7 @@ cudaError_t launch_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int6
         const cudaError_t e = p2_fft_post<T>(y, c, g, J, fm.tw, pp, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
+    if (pp.half) return cudaErrorNotSupported;       // half-channel output: power-of-two kernels only
     using C = cplx<T>;
     const int64_t n = g.M;
     const int64_t cap = tile_cap<T>();
@@ -297,6 +298,7 @@ cudaError_t launch_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int6
         const cudaError_t e = p2_pre_ifft<T>(c, y, g, J, fm.tw, pp, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
+    if (pp.half) return cudaErrorNotSupported;
     using C = cplx<T>;
     const int64_t n = g.M;
     const int64_t cap = tile_cap<T>();

@@ -315,10 +315,20 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>*
         C v[16];
         fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
         if (!ok) return;
-        C* cb = c + rm.base;
         const int rot = (int)rm.rot;
+        if (pp.half) {
+            // channels 0..N/2 of output row rm.base / N, rows of N/2 + 1
+            C* cb = c + (rm.base / N) * (N / 2 + 1);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) cb[(p2_out_pos<N>(t, i) + rot) & (N - 1)] = cmul(v[i], rm.ph);
+            for (int i = 0; i < 16; ++i) {
+                const int ch = (p2_out_pos<N>(t, i) + rot) & (N - 1);
+                if (ch <= N / 2) cb[ch] = cmul(v[i], rm.ph);
+            }
+        } else {
+            C* cb = c + rm.base;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cb[(p2_out_pos<N>(t, i) + rot) & (N - 1)] = cmul(v[i], rm.ph);
+        }
     }
 }
 
@@ -349,11 +359,25 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
     } else {
         RowMap<C> rm{};
         if (ok) rm = row_map(pp, g, b, j, nn);
-        const C* cb = c + (ok ? rm.base : 0);
         const int rot = (int)rm.rot;
-        fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
-            return ok ? cmulc(cb[(m + rot) & (N - 1)], rm.ph) : mk((T)0, (T)0);
-        }, v);
+        if (pp.half) {
+            // channel ch > N/2 is the conjugate of channel (-ch - 2 w(n)) mod N of the same column
+            const int64_t r_out = ok ? rm.base / N : 0;
+            const C* cb = c + r_out * (N / 2 + 1);
+            const int64_t n_out = r_out % pp.N;
+            const int tw2 = (int)((n_out * pp.lam1) % pp.lam2) * (int)(2 / pp.lam2);
+            fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                if (!ok) return mk((T)0, (T)0);
+                const int ch = (m + rot) & (N - 1);
+                C x = ch <= N / 2 ? cb[ch] : cconj(cb[(-ch - tw2) & (N - 1)]);
+                return cmulc(x, rm.ph);
+            }, v);
+        } else {
+            const C* cb = c + (ok ? rm.base : 0);
+            fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                return ok ? cmulc(cb[(m + rot) & (N - 1)], rm.ph) : mk((T)0, (T)0);
+            }, v);
+        }
     }
     if (!ok) return;
     C* yr = y + row * N;
@@ -452,6 +476,15 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void
         }
     }
     if (!ok) return;
+    if (fp.half) {
+        C* cr = c + row * (N / 2 + 1);                          // channels 0..N/2 only
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int pos = p2_out_pos<N>(t, i);
+            if (pos <= N / 2) cr[pos] = wn ? cmul(v[i], ph) : v[i];
+        }
+        return;
+    }
     C* cr = c + row * N;
     if (wn) {
 #pragma unroll
@@ -512,9 +545,19 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_p2(cons
             const bool ok = sidx < PR;
             const int r = q + D * sidx;
             const int64_t n = n0 + (ok ? r : 0);
-            const C* cr = c + (b * fp.N + n) * fp.M;
             C v[16];
-            fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C { return ok ? cr[m] : mk((T)0, (T)0); }, v);
+            if (fp.half) {
+                // channel m > N/2 is the conjugate of channel (-m - 2 w(n)) mod N
+                const C* cr = c + (b * fp.N + n) * (N / 2 + 1);
+                const int tw2 = (int)((n * fp.lam1) % fp.lam2) * (int)(2 / fp.lam2);
+                fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                    if (!ok) return mk((T)0, (T)0);
+                    return m <= N / 2 ? cr[m] : cconj(cr[(-m - tw2) & (N - 1)]);
+                }, v);
+            } else {
+                const C* cr = c + (b * fp.N + n) * fp.M;
+                fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C { return ok ? cr[m] : mk((T)0, (T)0); }, v);
+            }
             if (ok) {
                 const int wn = (int)((n * fp.lam1) % fp.lam2);
                 int64_t ln = fp.a * n - fp.center;

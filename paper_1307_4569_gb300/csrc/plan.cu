@@ -285,6 +285,7 @@ struct PlanCore {
     int64_t L1 = 0, L2 = 0;            // FFT_L split
     int64_t fir_cols = 0, fir_group = 1;
     bool fir_synth_ok = true;
+    bool fir_p2_synth = false;         // the FIR synthesis runs the power-of-two kernel
     std::vector<double> g_host;        // window as given (complex interleaved, float64)
     SepGeom coset_sep{};               // (lam2 a, M): used by the dual / tight Gram blocks
     int64_t ola_block = 0, ola_len = 0;  // blockwise plans: block length and local length
@@ -442,6 +443,8 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         pp.mN = make_mod((uint64_t)k.N);
         pp.m2N = make_mod(2 * (uint64_t)k.N);
         pp.mb = make_mod((uint64_t)k.b);
+        pp.lam1 = k.lam1;
+        pp.lam2 = k.lam2;
         if (k.route == DGT_ROUTE_COSET) {
             pp.mode = POST_COSET;
             pp.lam2 = k.lam2;
@@ -569,6 +572,10 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
 
     // ---- analysis ---------------------------------------------------------------------
     int exec(const void* f, int f_real, void* c, int64_t B, void* wsp, cudaStream_t st) override {
+        return exec_core(f, f_real, c, B, wsp, st, false);
+    }
+    // half: the coefficients hold channels 0..M/2 only (real signals; half_io checked)
+    int exec_core(const void* f, int f_real, void* c, int64_t B, void* wsp, cudaStream_t st, bool half) {
         const PlanCore& k = core;
         if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
         const Layout ly = layout(B);
@@ -579,6 +586,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         }
         if (k.route == DGT_ROUTE_FIR) {
             FirParams<C> fp = fir_params(0);
+            fp.half = half;
             KTRY("fir_analysis", st, launch_fir_analysis<T>(f, f_real, (C*)c, fp, *fft(k.M), B, st));
             return DGT_OK;
         }
@@ -605,7 +613,9 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             KTRY("zak_fwd", st, launch_zak_fwd<T>(zsrc, zreal, k.L, zf, k.L, k.L, k.sep.d, *fd, pre, B, st));
             KTRY("prod_ifft", st, launch_prod_ifft<T>(zf, (const C*)zg[0].p, k.J, y, k.sep, *fd, B, st));
         }
-        KTRY("fft_post", st, launch_fft_post<T>(y, (C*)c, k.sep, k.J, *fft(k.sep.M), post(), B, st));
+        PostParams<C> pp = post();
+        pp.half = half;
+        KTRY("fft_post", st, launch_fft_post<T>(y, (C*)c, k.sep, k.J, *fft(k.sep.M), pp, B, st));
         return DGT_OK;
     }
 
@@ -705,6 +715,9 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     }
 
     int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, cudaStream_t st) override {
+        return iexec_core(c, f, f_real, B, which, wsp, st, false);
+    }
+    int iexec_core(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, cudaStream_t st, bool half) {
         const PlanCore& k = core;
         if (which < 0 || which > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which);
         if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
@@ -723,13 +736,16 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
                 return fail(DGT_ERR_UNSUPPORTED, "FIR synthesis: %lld columns per tile cannot cover a window of %lld",
                             (long long)k.fir_cols, (long long)k.Lg);
             FirParams<C> fp = fir_params(which);
+            fp.half = half;
             KTRY("fir_synthesis", st, launch_fir_synthesis<T>((const C*)c, f, f_real, (C*)(ws + ly.seams), fp, *fft(k.M), B, st));
             return DGT_OK;
         }
         C* zf = (C*)(ws + ly.zf);
         C* y = (C*)(ws + ly.y);
         const FftRef* fd = fft(k.sep.d);
-        KTRY("pre_ifft", st, launch_pre_ifft<T>((const C*)c, y, k.sep, k.J, *fft(k.sep.M), post(), B, st));
+        PostParams<C> ppi = post();
+        ppi.half = half;
+        KTRY("pre_ifft", st, launch_pre_ifft<T>((const C*)c, y, k.sep, k.J, *fft(k.sep.M), ppi, B, st));
         KTRY("fft_prod_adj", st, launch_fft_prod_adj<T>(y, (const C*)zg[which].p, k.J, zf, k.sep, *fd, B, st));
         if (k.route == DGT_ROUTE_COSET) {
             KTRY("zak_inv", st, launch_zak_inv<T>(zf, k.L, f, f_real, k.L, k.L, k.sep.d, *fd, nochirp(), (T)1, B, st));
@@ -812,11 +828,23 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         CUDA_TRY(cudaGetLastError());
         return DGT_OK;
     }
+    // the power-of-two kernels read / write channels 0..M/2 directly: the FIR kernels, and
+    // the channel FFT of the coset and time-shear routes (analysis) or its adjoint (synthesis)
+    bool half_io(bool synthesis) const {
+        const PlanCore& k = core;
+        const bool p2row = k.M >= 128 && (k.M & (k.M - 1)) == 0 && k.M <= (int64_t)(sizeof(T) == 4 ? 16384 : 8192);
+        if (k.route == DGT_ROUTE_FIR) return p2row && k.M <= 8192 && (!synthesis || k.fir_p2_synth);
+        return p2row && !k.freq_shear && k.sep.M == k.M;
+    }
     int exec_real(const void* f, void* ch, int64_t B, cudaStream_t st) override {
-        return exec_real_via<T>(this, f, ch, B, st);
+        if (!half_io(false)) return exec_real_via<T>(this, f, ch, B, st);
+        DGT_TRY(real_ok(core));
+        return exec_core(f, 1, ch, B, nullptr, st, true);
     }
     int iexec_real(const void* ch, void* f, int64_t B, int which, cudaStream_t st) override {
-        return iexec_real_via<T>(this, ch, f, B, which, st);
+        if (!half_io(true)) return iexec_real_via<T>(this, ch, f, B, which, st);
+        DGT_TRY(real_ok(core));
+        return iexec_core(ch, f, 1, B, which, nullptr, st, true);
     }
 
     // FIR synthesis whose seam scratch is the library's fixed per-GPU array: no allocation.
@@ -919,6 +947,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
     // synthesis also needs a * cols >= Lg - a so that only neighbouring chunks overlap
     int64_t fir_cols = 0, fir_group = 1;
     bool fir_synth_ok = false;
+    bool fir_p2 = false;
     if (g->kind == DGT_WINDOW_FIR && fft_ok(M, precision)) {
         const size_t csz = precision == DGT_F64 ? 16 : 8;
         const int64_t need = std::max<int64_t>(1, (g->len + a - 1) / a);
@@ -945,6 +974,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
             fir_cols = cols2;
             fir_synth_ok = true;
             fir_group = 1;
+            fir_p2 = true;
         }
     }
     if (route == DGT_ROUTE_AUTO) {
@@ -976,6 +1006,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
         k.fir_cols = fir_cols;
         k.fir_group = fir_group;
         k.fir_synth_ok = fir_synth_ok;
+        k.fir_p2_synth = fir_p2;
     } else if (route == DGT_ROUTE_COSET) {
         k.sep = make_sep(L, lam2 * a, M);
         k.J = lam2;
