@@ -97,7 +97,7 @@ typedef struct {
 int dgt_plan_create(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t lambda1, int64_t lambda2,
                     const dgt_window* g, int route, int precision, void* stream);
 
-/* Blockwise (overlap-add) plan for an FIR window: Section 3 (the OLA algorithm) and Section 4
+/* Blockwise (overlap-add) plan for an FIR window: Section 4 (the OLA algorithm) and Section 4.1
  * (the shear-OLA algorithm).  The signal is cut into L / block_len blocks; each block,
  * zero-extended to Lx = the smallest multiple of lambda2 * lcm(a, M) not below
  * block_len + g->len whose transform this build supports (reported as ola_len by
@@ -137,7 +137,7 @@ int dgt_exec(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t bat
 int idgt_exec(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
               void* stream);
 
-/* Real-signal coefficients (the real-signal variant of the interface, Section 5): for a real
+/* Real-signal coefficients (the real-signal variant of the interface, Section 4.4): for a real
  * signal and a real window on a lattice with lambda2 <= 2 and M even,
  * c(m, n) = conj(c((-m - 2 w(n)) mod M, n)), so the channels 0..M/2 determine c.
  * dgt_exec_real: f DEVICE [batch][L] real -> c DEVICE [batch][N][M/2 + 1] complex.

@@ -8,7 +8,7 @@ For a real signal f and a real window g, eq. DGT gives
 (indices modulo M).  With lambda2 <= 2, 2 w(n) = (n lambda1) mod lambda2 is an integer, so
 every channel is the conjugate of a channel at most M/2 ... the channels 0..M/2 (M even)
 determine c.  This is the real-signal variant of the library interface the paper uses
-(LTFAT's dgtreal, Section 5); the symmetry holds for lambda2 <= 2 only.
+(LTFAT's dgtreal, Section 4.4); the symmetry holds for lambda2 <= 2 only.
 """
 from __future__ import annotations
 

@@ -3,7 +3,7 @@
 Test infrastructure only: imported by tests/, __graft_entry__.smoke() and the CPU legs of
 bench.py; shares no code with the CUDA path.
 
-The OLA algorithm (Section 3, and the shear-OLA algorithm of Section 4): the signal of
+The OLA algorithm (Section 4, and the shear-OLA algorithm of Section 4.1): the signal of
 length L = Lb Nb is cut into Nb blocks of Lb samples; every block, zero-extended to a length
 Lx >= Lb + Lg (Lg the window support), is transformed with the same lattice and window on
 Z_Lx, and the coefficient columns of the short transforms are added into the columns of the

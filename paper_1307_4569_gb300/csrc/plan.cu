@@ -1064,7 +1064,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
 }
 
 // ---------------------------------------------------------------------------------------
-// Blockwise (overlap-add) plan (Section 3, OLA; Section 4, shear-OLA): blocks of Lb samples,
+// Blockwise (overlap-add) plan (Section 4, OLA; Section 4.1, shear-OLA): blocks of Lb samples,
 // zero-extended to Lx, transformed by a full-window plan of length Lx, their coefficient
 // columns added into the long transform's columns (and the adjoint for synthesis).
 // ---------------------------------------------------------------------------------------
