@@ -3,7 +3,7 @@
 Test infrastructure only: imported by tests/, __graft_entry__.smoke() and the CPU legs of
 bench.py; shares no code with the CUDA path.
 
-Section 3.2 (extension to higher dimensions): with a separable window g1 (x) g2 and a lattice
+Section 3.5 (extension to higher dimensions): with a separable window g1 (x) g2 and a lattice
 Lambda1 x Lambda2 (each nonseparable on its own axis), the transform of f(l1, l2) is
 
     c(m1, n1, m2, n2) = sum_{l1, l2} f(l1, l2) conj(g1(l1 - a1 n1)) conj(g2(l2 - a2 n2))
