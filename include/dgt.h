@@ -117,6 +117,27 @@ int dgt_plan_create(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t l
 int dgt_plan_create_ola(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64_t lambda1, int64_t lambda2,
                         const dgt_window* g, int64_t block_len, int inner_route, int precision, void* stream);
 
+/* Two-dimensional DGT on a tensor-product lattice Lambda1 x Lambda2 with a separable window
+ * g1 (x) g2 (Section 3.5, extension to higher dimensions): each axis is a lattice of its own
+ * (L_i, a_i, M_i, lambda_i1 / lambda_i2, window g_i, one dgt_plan_create each, same route
+ * and precision), and the transform is the second axis' DGT of every row followed by the
+ * first axis' DGT of every column.  Signals f: DEVICE [batch][L1][L2] (real or complex);
+ * coefficients c: DEVICE [batch][N1][M1][N2][M2] complex, i.e. c(m1, n1, m2, n2) at
+ * ((n1 M1 + m1) N2 + n2) M2 + m2.  idgt2_exec: synthesis with g1 (x) g2 (adjoint), or the
+ * tensor product of the axes' dual / tight windows (which_window as for idgt_exec).
+ * Work arrays (2 B L1 N2 M2 + B N1 M1 N2 M2 complex) are plan-owned.  Errors: those of
+ * dgt_plan_create for either axis, and of dgt_exec / idgt_exec. */
+typedef struct dgt2_plan_s* dgt2_plan_t;
+int dgt2_plan_create(dgt2_plan_t* plan, int64_t L1, int64_t a1, int64_t M1, int64_t lambda11, int64_t lambda12,
+                     const dgt_window* g1, int64_t L2, int64_t a2, int64_t M2, int64_t lambda21, int64_t lambda22,
+                     const dgt_window* g2, int route, int precision, void* stream);
+int dgt2_exec(dgt2_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* stream);
+int idgt2_exec(dgt2_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window, void* stream);
+/* Synchronise `stream` and report a pending asynchronous error of either axis' work. */
+int dgt2_plan_status(dgt2_plan_t plan, void* stream);
+/* Release the plan (synchronises the device first). */
+void dgt2_plan_destroy(dgt2_plan_t plan);
+
 /* Copy the resolved plan parameters into *info. */
 int dgt_plan_get_info(dgt_plan_t plan, dgt_plan_info* info);
 

@@ -48,6 +48,12 @@ vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
 SIGNATURES = {
     "dgt_plan_create": (i32, [C.POINTER(vp), i64, i64, i64, i64, i64, C.POINTER(Window), i32, i32, vp]),
     "dgt_plan_create_ola": (i32, [C.POINTER(vp), i64, i64, i64, i64, i64, C.POINTER(Window), i64, i32, i32, vp]),
+    "dgt2_plan_create": (i32, [C.POINTER(vp), i64, i64, i64, i64, i64, C.POINTER(Window),
+                               i64, i64, i64, i64, i64, C.POINTER(Window), i32, i32, vp]),
+    "dgt2_exec": (i32, [vp, vp, i32, vp, i64, vp]),
+    "idgt2_exec": (i32, [vp, vp, vp, i32, i64, i32, vp]),
+    "dgt2_plan_status": (i32, [vp, vp]),
+    "dgt2_plan_destroy": (None, [vp]),
     "dgt_plan_get_info": (i32, [vp, C.POINTER(PlanInfo)]),
     "dgt_plan_set_window": (i32, [vp, vp, i32, vp]),
     "dgt_exec": (i32, [vp, vp, i32, vp, i64, vp]),

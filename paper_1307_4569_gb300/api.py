@@ -197,6 +197,74 @@ class Plan:
         return v.value
 
 
+def _window_struct(window, fir_center):
+    w = np.asarray(window.detach().cpu().numpy() if torch.is_tensor(window) else window)
+    real = not np.iscomplexobj(w)
+    data = np.ascontiguousarray(w.astype(np.float64) if real else w.astype(np.complex128).view(np.float64))
+    win = K.Window(K.WINDOW_FIR if fir_center is not None else K.WINDOW_FULL, len(w), int(fir_center or 0),
+                   data.ctypes.data_as(C.POINTER(C.c_double)), int(real))
+    return win, data
+
+
+class Plan2:
+    """Two-dimensional DGT on the tensor-product lattice lattice1 x lattice2 with the separable
+    window g1 (x) g2 (dgt2_plan_create).  lattice_i = (L_i, a_i, M_i, lam1_i, lam2_i); signals
+    f[..., L1, L2]; coefficients c[..., N1, M1, N2, M2]."""
+
+    def __init__(self, lattice1, window1, lattice2, window2, route="auto", precision="f32", fir_center1=None,
+                 fir_center2=None, stream=None):
+        (L1, a1, M1, p1, q1), (L2, a2, M2, p2, q2) = lattice1, lattice2
+        w1, d1 = _window_struct(window1, fir_center1)
+        w2, d2 = _window_struct(window2, fir_center2)
+        self._keep = (d1, d2)
+        prec = K.F64 if precision == "f64" else K.F32
+        h = C.c_void_p()
+        K.check(K.lib().dgt2_plan_create(C.byref(h), L1, a1, M1, p1, q1, C.byref(w1), L2, a2, M2, p2, q2, C.byref(w2),
+                                          _ROUTES[route], prec, _stream(stream)))
+        self._h = h
+        self.L1, self.L2, self.N1, self.M1, self.N2, self.M2 = L1, L2, L1 // a1, M1, L2 // a2, M2
+        self.precision = precision
+        self.rdtype = torch.float64 if precision == "f64" else torch.float32
+        self.cdtype = torch.complex128 if precision == "f64" else torch.complex64
+
+    def close(self):
+        if getattr(self, "_h", None):
+            K.lib().dgt2_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dgt(self, f: torch.Tensor, stream=None) -> torch.Tensor:
+        if not f.is_cuda or not f.is_contiguous() or f.dtype not in (self.rdtype, self.cdtype):
+            raise TypeError("signals must be contiguous CUDA tensors of the plan precision")
+        if tuple(f.shape[-2:]) != (self.L1, self.L2):
+            raise ValueError("signal shape %s != (L1, L2)" % (tuple(f.shape),))
+        B = int(np.prod(f.shape[:-2])) if f.dim() > 2 else 1
+        out = torch.empty(tuple(f.shape[:-2]) + (self.N1, self.M1, self.N2, self.M2), dtype=self.cdtype,
+                          device=f.device)
+        K.check(K.lib().dgt2_exec(self._h, f.data_ptr(), int(not f.is_complex()), out.data_ptr(), B, _stream(stream)))
+        return out
+
+    def idgt(self, c: torch.Tensor, window: str = "dual", real: bool = False, stream=None) -> torch.Tensor:
+        if not c.is_cuda or not c.is_contiguous() or c.dtype != self.cdtype:
+            raise TypeError("coefficients must be a contiguous CUDA %s tensor" % self.cdtype)
+        if tuple(c.shape[-4:]) != (self.N1, self.M1, self.N2, self.M2):
+            raise ValueError("coefficient shape %s != (N1, M1, N2, M2)" % (tuple(c.shape),))
+        B = int(np.prod(c.shape[:-4])) if c.dim() > 4 else 1
+        out = torch.empty(tuple(c.shape[:-4]) + (self.L1, self.L2), dtype=self.rdtype if real else self.cdtype,
+                          device=c.device)
+        K.check(K.lib().idgt2_exec(self._h, c.data_ptr(), out.data_ptr(), int(real), B, _SYN[window],
+                                   _stream(stream)))
+        return out
+
+    def status(self, stream=None) -> None:
+        K.check(K.lib().dgt2_plan_status(self._h, _stream(stream)))
+
+
 def fft_selftest(x: torch.Tensor, direction: int = -1) -> torch.Tensor:
     """Library FFT building block on rows of x (contiguous complex CUDA tensor)."""
     prec = K.F64 if x.dtype == torch.complex128 else K.F32

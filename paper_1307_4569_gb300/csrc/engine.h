@@ -159,6 +159,10 @@ template <typename T>
 cudaError_t launch_half_expand(const cplx<T>* half, cplx<T>* full, int64_t N, int64_t M, int64_t lam1, int64_t lam2,
                                int64_t B, cudaStream_t st);
 
+// batched transpose [B][R][Cc] -> [B][Cc][R]
+template <typename T>
+cudaError_t launch_transpose(const cplx<T>* in, cplx<T>* out, int64_t R, int64_t Cc, int64_t B, cudaStream_t st);
+
 // elementwise helpers
 template <typename T>
 cudaError_t launch_coset_windows(const cplx<T>* g, cplx<T>* gj, int64_t L, int64_t a, int64_t J, const int64_t* sigma,

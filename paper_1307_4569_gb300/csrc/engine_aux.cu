@@ -700,6 +700,39 @@ template cudaError_t launch_half_expand<double>(const double2*, double2*, int64_
                                                 cudaStream_t);
 
 // =====================================================================================
+// Batched transpose [B][R][Cc] -> [B][Cc][R] of complex arrays through 32 x 33 shared tiles
+// (the two-dimensional transform applies each axis' plan to contiguous rows)
+// =====================================================================================
+template <typename C>
+__global__ void __launch_bounds__(256) transpose_kernel(const C* __restrict__ in, C* __restrict__ out, int64_t R,
+                                                        int64_t Cc) {
+    __shared__ C tile[32][33];
+    const int64_t b = blockIdx.z;
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const C* src = in + b * R * Cc;
+    C* dst = out + b * R * Cc;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t r = r0 + i, cc = c0 + threadIdx.x;
+        if (r < R && cc < Cc) tile[i][threadIdx.x] = src[r * Cc + cc];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t cc = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && cc < Cc) dst[cc * R + r] = tile[threadIdx.x][i];
+    }
+}
+
+template <typename T>
+cudaError_t launch_transpose(const cplx<T>* in, cplx<T>* out, int64_t R, int64_t Cc, int64_t B, cudaStream_t st) {
+    if (B <= 0 || R <= 0 || Cc <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((Cc + 31) / 32), (unsigned)((R + 31) / 32), (unsigned)B);
+    transpose_kernel<cplx<T>><<<grid, dim3(32, 8), 0, st>>>(in, out, R, Cc);
+    return cudaGetLastError();
+}
+template cudaError_t launch_transpose<float>(const float2*, float2*, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_transpose<double>(const double2*, double2*, int64_t, int64_t, int64_t, cudaStream_t);
+
+// =====================================================================================
 // Scratch of the allocation-free FIR synthesis entry point: one fixed array per GPU that
 // loads the library, held until the process exits.  Host code must not use the symbol as
 // a pointer: its device address comes from cudaGetSymbolAddress, looked up once per device.

@@ -1215,6 +1215,45 @@ static int create_ola_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int
 }
 
 // ---------------------------------------------------------------------------------------
+// Two-dimensional DGT on a tensor-product lattice (Section 3.5): the plan of the second axis
+// on every row, a transpose, the plan of the first axis on every column of the result, a
+// transpose; synthesis in the reverse order.
+// ---------------------------------------------------------------------------------------
+struct dgt2_plan_s {
+    std::unique_ptr<dgt_plan_s> p1, p2;   // first axis (L1), second axis (L2)
+    int64_t L1 = 0, L2 = 0, K1 = 0, K2 = 0;   // K = N M coefficients per axis
+    int precision = DGT_F32;
+    DevBuf work;
+    static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+    template <typename T> int exec(const void* f, int f_real, void* c, int64_t B, cudaStream_t st) {
+        using C = cplx<T>;
+        const size_t n12 = (size_t)B * L1 * K2, n3 = (size_t)B * K1 * K2;
+        DGT_TRY(work.alloc(2 * al(sizeof(C) * n12) + al(sizeof(C) * n3)));
+        C* t1 = (C*)work.p;
+        C* t2 = (C*)((char*)work.p + al(sizeof(C) * n12));
+        C* t3 = (C*)((char*)work.p + 2 * al(sizeof(C) * n12));
+        DGT_TRY(p2->exec(f, f_real, t1, B * L1, nullptr, st));                 // rows: [B][L1][N2 M2]
+        KTRY("transpose", st, launch_transpose<T>(t1, t2, L1, K2, B, st));      // [B][N2 M2][L1]
+        DGT_TRY(p1->exec(t2, 0, t3, B * K2, nullptr, st));                      // [B][N2 M2][N1 M1]
+        KTRY("transpose", st, launch_transpose<T>(t3, (C*)c, K2, K1, B, st));   // [B][N1 M1][N2 M2]
+        return DGT_OK;
+    }
+    template <typename T> int iexec(const void* c, void* f, int f_real, int64_t B, int which, cudaStream_t st) {
+        using C = cplx<T>;
+        const size_t n12 = (size_t)B * L1 * K2, n3 = (size_t)B * K1 * K2;
+        DGT_TRY(work.alloc(2 * al(sizeof(C) * n12) + al(sizeof(C) * n3)));
+        C* t1 = (C*)work.p;
+        C* t2 = (C*)((char*)work.p + al(sizeof(C) * n12));
+        C* t3 = (C*)((char*)work.p + 2 * al(sizeof(C) * n12));
+        KTRY("transpose", st, launch_transpose<T>((const C*)c, t3, K1, K2, B, st));   // [B][N2 M2][N1 M1]
+        DGT_TRY(p1->iexec(t3, t2, 0, B * K2, which, nullptr, st));                   // [B][N2 M2][L1]
+        KTRY("transpose", st, launch_transpose<T>(t2, t1, K2, L1, B, st));           // [B][L1][N2 M2]
+        return p2->iexec(t1, f, f_real, B * L1, which, nullptr, st);                 // [B][L1][L2]
+    }
+};
+
+// ---------------------------------------------------------------------------------------
 // extern "C"
 // ---------------------------------------------------------------------------------------
 extern "C" {
@@ -1236,6 +1275,56 @@ int dgt_plan_create_ola(dgt_plan_t* plan, int64_t L, int64_t a, int64_t M, int64
     } catch (const std::bad_alloc&) {
         return fail(DGT_ERR_OOM, "host allocation failed");
     }
+}
+
+int dgt2_plan_create(dgt2_plan_t* plan, int64_t L1, int64_t a1, int64_t M1, int64_t lam11, int64_t lam12,
+                     const dgt_window* g1, int64_t L2, int64_t a2, int64_t M2, int64_t lam21, int64_t lam22,
+                     const dgt_window* g2, int route, int precision, void* stream) {
+    if (!plan) return fail(DGT_ERR_ARG, "null plan pointer");
+    *plan = nullptr;
+    try {
+        dgt_plan_t q1 = nullptr, q2 = nullptr;
+        DGT_TRY(create_plan(&q1, L1, a1, M1, lam11, lam12, g1, route, precision, (cudaStream_t)stream));
+        std::unique_ptr<dgt_plan_s> h1(q1);
+        DGT_TRY(create_plan(&q2, L2, a2, M2, lam21, lam22, g2, route, precision, (cudaStream_t)stream));
+        auto* p = new dgt2_plan_s();
+        p->p1 = std::move(h1);
+        p->p2.reset(q2);
+        p->L1 = L1; p->L2 = L2;
+        p->K1 = (L1 / a1) * M1; p->K2 = (L2 / a2) * M2;
+        p->precision = precision;
+        *plan = p;
+        return DGT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(DGT_ERR_OOM, "host allocation failed");
+    }
+}
+
+int dgt2_exec(dgt2_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    if (batch <= 0) return batch == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+    return plan->precision == DGT_F64 ? plan->exec<double>(f, f_is_real, c, batch, (cudaStream_t)stream)
+                                      : plan->exec<float>(f, f_is_real, c, batch, (cudaStream_t)stream);
+}
+
+int idgt2_exec(dgt2_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    if (which_window < 0 || which_window > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which_window);
+    if (batch <= 0) return batch == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+    return plan->precision == DGT_F64 ? plan->iexec<double>(c, f, f_real_out, batch, which_window, (cudaStream_t)stream)
+                                      : plan->iexec<float>(c, f, f_real_out, batch, which_window, (cudaStream_t)stream);
+}
+
+int dgt2_plan_status(dgt2_plan_t plan, void* stream) {
+    if (!plan) return fail(DGT_ERR_ARG, "null plan");
+    DGT_TRY(plan->p1->status_check((cudaStream_t)stream));
+    return plan->p2->status_check((cudaStream_t)stream);
+}
+
+void dgt2_plan_destroy(dgt2_plan_t plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    delete plan;
 }
 
 int dgt_plan_get_info(dgt_plan_t plan, dgt_plan_info* info) {
