@@ -283,7 +283,7 @@ __device__ __forceinline__ RowMap<C> row_map(const PostParams<C>& pp, const SepG
 // per-coefficient index map of the frequency-shear branch; the other modes need one
 // (base, rotation, phase) per row, computed before the transform so that it is not live
 // beside the 16 values.  Separate instantiations keep the register budget of each.
-template <typename T, int N, bool SH1>
+template <typename T, int N, bool SH1, bool HALF>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>* __restrict__ y,
                                                                   cplx<T>* __restrict__ c, SepGeom g, int64_t J,
                                                                   int64_t rows_total, const cplx<T>* __restrict__ tw,
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>*
         fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
         if (!ok) return;
         const int rot = (int)rm.rot;
-        if (pp.half) {
+        if constexpr (HALF) {
             // channels 0..N/2 of output row rm.base / N, rows of N/2 + 1
             C* cb = c + (rm.base / N) * (N / 2 + 1);
 #pragma unroll
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>*
 }
 
 // pre_ifft: gather c with conjugate phases, unnormalised inverse FFT, store rows of Y
-template <typename T, int N, bool SH1>
+template <typename T, int N, bool SH1, bool HALF>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>* __restrict__ c,
                                                                   cplx<T>* __restrict__ y, SepGeom g, int64_t J,
                                                                   int64_t rows_total, const cplx<T>* __restrict__ tw,
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
         RowMap<C> rm{};
         if (ok) rm = row_map(pp, g, b, j, nn);
         const int rot = (int)rm.rot;
-        if (pp.half) {
+        if constexpr (HALF) {
             // channel ch > N/2 is the conjugate of channel (-ch - 2 w(n)) mod N of the same column
             const int64_t r_out = ok ? rm.base / N : 0;
             const C* cb = c + r_out * (N / 2 + 1);
@@ -679,7 +679,9 @@ cudaError_t p2_fft_post_n(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_
                           const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
     using RC = RowCfg<N>;
     const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
-    auto k = pp.mode == POST_SHEAR1 ? fft_post_p2<T, N, true> : fft_post_p2<T, N, false>;
+    if (pp.half && pp.mode == POST_SHEAR1) return cudaErrorNotSupported;
+    auto k = pp.mode == POST_SHEAR1 ? fft_post_p2<T, N, true, false>
+                                    : pp.half ? fft_post_p2<T, N, false, true> : fft_post_p2<T, N, false, false>;
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     const int64_t rows = B * J * g.d * g.q;
@@ -695,7 +697,9 @@ cudaError_t p2_pre_ifft_n(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_
                           const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
     using RC = RowCfg<N>;
     const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
-    auto k = pp.mode == POST_SHEAR1 ? pre_ifft_p2<T, N, true> : pre_ifft_p2<T, N, false>;
+    if (pp.half && pp.mode == POST_SHEAR1) return cudaErrorNotSupported;
+    auto k = pp.mode == POST_SHEAR1 ? pre_ifft_p2<T, N, true, false>
+                                    : pp.half ? pre_ifft_p2<T, N, false, true> : pre_ifft_p2<T, N, false, false>;
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     const int64_t rows = B * J * g.d * g.q;
