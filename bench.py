@@ -263,23 +263,26 @@ def run_ours(args, rank, world):
 
     # ---------------- end to end through the public API, pinned host buffers ----------------
     # Every step copies the signals in from pinned host memory and every route's coefficients
-    # and reconstruction back out.  Each route's results leave on a copy stream of its own, so
-    # the device-to-host traffic of one route overlaps the transforms of the next.
+    # and reconstruction back out.  The results leave on one copy stream, route after route, so
+    # the device-to-host traffic of one route overlaps the transforms of the next (copies of
+    # several routes in flight at once on separate streams shared the link badly: 3-4x slower).
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     nroutes = len(plans)
     c_hosts = [torch.empty((B, w.N, w.M), dtype=torch.complex64).pin_memory() for _ in range(nroutes)]
     fr_hosts = [torch.empty((B, w.L), dtype=torch.float32).pin_memory() for _ in range(nroutes)]
+    d2h_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nroutes)]
     cbufs = [cbuf] + [torch.empty_like(cbuf) for _ in range(nroutes - 1)]
     frs = [fr] + [torch.empty_like(fr) for _ in range(nroutes - 1)]
-    copy_streams = [torch.cuda.Stream(dev) for _ in range(nroutes)]
+    cs = torch.cuda.Stream(dev)
+    copied = [None] * nroutes                    # per route: its buffers' copies are done
     fin = torch.empty_like(f)
 
     def e2e_step():
         cur = torch.cuda.current_stream(dev)
         fin.copy_(f_host, non_blocking=True)
         for r, (_, p) in enumerate(plans):
-            cs = copy_streams[r]
-            cur.wait_stream(cs)                  # the previous step's copies of this route's buffers
+            if copied[r] is not None:
+                cur.wait_event(copied[r])        # the previous step's copies of this route's buffers
             p.dgt(fin, out=cbufs[r])
             e_c = torch.cuda.Event()
             e_c.record(cur)
@@ -288,11 +291,14 @@ def run_ours(args, rank, world):
             e_f.record(cur)
             with torch.cuda.stream(cs):
                 cs.wait_event(e_c)
+                d2h_ev[r][0].record(cs)
                 c_hosts[r].copy_(cbufs[r], non_blocking=True)
+                d2h_ev[r][1].record(cs)
                 cs.wait_event(e_f)
                 fr_hosts[r].copy_(frs[r], non_blocking=True)
-        for cs in copy_streams:                  # the step ends when its results are on the host
-            cur.wait_stream(cs)
+                copied[r] = torch.cuda.Event()
+                copied[r].record(cs)
+        cur.wait_stream(cs)                      # the step ends when its results are on the host
 
     e2e_step()
     torch.cuda.synchronize()
@@ -306,6 +312,7 @@ def run_ours(args, rank, world):
     a1.record()
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(a0.elapsed_time(a1) / e2e_steps, world, dev)
+    d2h_ms = [e0.elapsed_time(e1) for e0, e1 in d2h_ev]          # last step, per route
     te = time.time()
     clocks.stop()
     clk = clocks.summary(t0, te)
@@ -385,7 +392,8 @@ def run_ours(args, rank, world):
         "kernels": kernels,
         "gpu_launches": launches * 1 if launches else 0,
         "e2e": {"value": world * coefs_per_step / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
-                "steps": e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "steps": e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "coef_copy_ms_per_route": d2h_ms},
         "fp64": fp64,
         "clocks": clk,
         "reconstruction_rel_err": err,

@@ -19,6 +19,20 @@ __host__ __device__ __forceinline__ double2 mk(double x, double y) { return make
 
 template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
 template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000 && !defined(DGT_SCALAR_F32)
+#define DGT_PACKED_F32 1
+// float: one packed two-lane instruction per complex addition (same rounding per lane as the
+// scalar forms; a - b is the fused b * (-1) + a, which is exact before its one rounding).
+// -DDGT_SCALAR_F32 builds the scalar forms instead.
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+// a + s i b for s = +-1: (a.x - s b.y, a.y + s b.x), one packed fused multiply-add
+template <int S> __device__ __forceinline__ float2 cadd_ib(float2 a, float2 b) {
+    return __ffma2_rn(make_float2(b.y, b.x), make_float2((float)-S, (float)S), a);
+}
+#endif
 template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
     C r;
     r.x = a.x * b.x - a.y * b.y;
@@ -33,7 +47,14 @@ template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
     return r;
 }
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
-template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) {
+#ifdef DGT_PACKED_F32
+    if constexpr (sizeof(C) == 8) return __fmul2_rn(a, make_float2((float)s, (float)s));
+#endif
+    a.x *= s;
+    a.y *= s;
+    return a;
+}
 // multiply by +i (DIR=+1) or -i (DIR=-1)
 template <int DIR, typename C> __host__ __device__ __forceinline__ C mul_i(C a) {
     C r;

@@ -33,6 +33,16 @@ template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) 
 
 template <int DIR, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
     C s02 = cadd(x0, x2), d02 = csub(x0, x2);
+#ifdef DGT_PACKED_F32
+    if constexpr (sizeof(C) == 8) {
+        const C s13 = cadd(x1, x3), d13 = csub(x1, x3);
+        x0 = cadd(s02, s13);
+        x2 = csub(s02, s13);
+        x1 = cadd_ib<DIR>(d02, d13);
+        x3 = cadd_ib<-DIR>(d02, d13);
+        return;
+    }
+#endif
     C s13 = cadd(x1, x3), d13 = mul_i<DIR>(csub(x1, x3));
     x0 = cadd(s02, s13);
     x2 = csub(s02, s13);

@@ -391,11 +391,12 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
 // SEG: the RPB columns of a CTA are consecutive columns of one signal; their common segment
 // of (RPB - 1) a + Lg samples is first copied to shared memory with coalesced loads, and the
 // taps are gathered from there.
+// MULTI: windows longer than N (several taps per bin).  Float with Lg <= N is held to 64
+// registers, the occupancy of the other row kernels.
 template <typename T, int N, bool MULTI, bool SEG>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS) fir_analysis_p2(const void* __restrict__ f, int f_real,
-                                                                      cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
-                                                                      int64_t rows_total,
-                                                                      const cplx<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(RowCfg<N>::THREADS, sizeof(T) == 4 && !MULTI ? RowCfg<N>::MINB : 1)
+    fir_analysis_p2(const void* __restrict__ f, int f_real, cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
+                    int64_t rows_total, const cplx<T>* __restrict__ tw) {
     using C = cplx<T>;
     using RC = RowCfg<N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
