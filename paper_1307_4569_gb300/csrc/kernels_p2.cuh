@@ -29,6 +29,19 @@ template <typename T, int N> struct ColCfg {
     static_assert(W >= 1, "tile does not fit");
 };
 
+// fft_prod_adj (two sets of 16 values per thread, the transform and the accumulators): float
+// tiles of half the columns, two CTAs per SM (<= 128 registers), so that one CTA computes while
+// the other waits at an exchange barrier (2.32 -> 2.16 ms on 64 audio signals; zak_prod_ifft,
+// which holds its Zak column the same way, got slower with it and keeps the full tiles)
+template <typename T, int N> struct AdjCfg {
+    using Base = ColCfg<T, N>;
+    static constexpr bool HALVE = sizeof(T) == 4 && N >= 1024 && Base::W >= 2;
+    static constexpr int W = HALVE ? Base::W / 2 : Base::W;
+    static constexpr int THREADS = W * Base::G;
+    static constexpr size_t SMEM = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * W;
+    static constexpr int MINB = HALVE ? 2 : 1;
+};
+
 template <int N> struct RowCfg {
     static constexpr int G = N / 16;
     static constexpr int RPB = G >= 256 ? 1 : 256 / G;                   // rows per CTA
@@ -115,12 +128,12 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MINB) pro
 // ZG~_j[xi][k - a w], summed into ZF'[b][xi][k].   grid (k-blocks, B)
 // ------------------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(ColCfg<T, N>::THREADS) fft_prod_adj_p2(const cplx<T>* __restrict__ y,
+__global__ void __launch_bounds__(AdjCfg<T, N>::THREADS, AdjCfg<T, N>::MINB) fft_prod_adj_p2(const cplx<T>* __restrict__ y,
                                                                          const cplx<T>* __restrict__ zg,
                                                                          cplx<T>* __restrict__ zf, SepGeom g,
                                                                          int64_t J, const cplx<T>* __restrict__ tw) {
     using C = cplx<T>;
-    using CF = ColCfg<T, N>;
+    using CF = AdjCfg<T, N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
@@ -653,7 +666,7 @@ cudaError_t p2_prod_ifft_n(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx
 template <typename T, int N>
 cudaError_t p2_fft_prod_adj_n(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
                               const void* tw, int64_t B, cudaStream_t st) {
-    using CF = ColCfg<T, N>;
+    using CF = AdjCfg<T, N>;
     auto k = fft_prod_adj_p2<T, N>;
     const size_t smem = CF::SMEM;
     cudaError_t e = p2_smem(k, smem);
