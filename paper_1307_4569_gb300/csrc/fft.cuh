@@ -25,16 +25,31 @@ struct FftPlanDev {
 // ---------------------------------------------------------------------------------
 // small DFTs in registers:  X[k] = sum_r x[r] exp(DIR 2 pi i r k / R)
 // ---------------------------------------------------------------------------------
-template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
-    C t = a;
-    a = cadd(t, b);
-    b = csub(t, b);
+// PK = false keeps the float complex additions of the power-of-two codelets scalar (for a kernel
+// that runs faster that way; the packed forms are the default)
+template <bool PK, typename C> __device__ __forceinline__ C kadd(C a, C b) {
+    if constexpr (PK) return cadd(a, b);
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+template <bool PK, typename C> __device__ __forceinline__ C ksub(C a, C b) {
+    if constexpr (PK) return csub(a, b);
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
 }
 
-template <int DIR, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
-    C s02 = cadd(x0, x2), d02 = csub(x0, x2);
+template <int DIR, bool PK = true, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+    C t = a;
+    a = kadd<PK>(t, b);
+    b = ksub<PK>(t, b);
+}
+
+template <int DIR, bool PK = true, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
+    C s02 = kadd<PK>(x0, x2), d02 = ksub<PK>(x0, x2);
 #ifdef DGT_PACKED_F32
-    if constexpr (sizeof(C) == 8) {
+    if constexpr (PK && sizeof(C) == 8) {
         const C s13 = cadd(x1, x3), d13 = csub(x1, x3);
         x0 = cadd(s02, s13);
         x2 = csub(s02, s13);
@@ -43,11 +58,11 @@ template <int DIR, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1
         return;
     }
 #endif
-    C s13 = cadd(x1, x3), d13 = mul_i<DIR>(csub(x1, x3));
-    x0 = cadd(s02, s13);
-    x2 = csub(s02, s13);
-    x1 = cadd(d02, d13);
-    x3 = csub(d02, d13);
+    C s13 = kadd<PK>(x1, x3), d13 = mul_i<DIR>(ksub<PK>(x1, x3));
+    x0 = kadd<PK>(s02, s13);
+    x2 = ksub<PK>(s02, s13);
+    x1 = kadd<PK>(d02, d13);
+    x3 = ksub<PK>(d02, d13);
 }
 
 // multiply by exp(DIR 2 pi i E / 16) for a compile-time E in 0..15
@@ -70,36 +85,36 @@ template <int DIR, int E, typename C> __device__ __forceinline__ C w16(C x) {
     }
 }
 
-template <int DIR, typename C> __device__ __forceinline__ void dft8(C* v) {
+template <int DIR, bool PK = true, typename C> __device__ __forceinline__ void dft8(C* v) {
     // even/odd split: E = DFT4(v0,v2,v4,v6), O = DFT4(v1,v3,v5,v7), X[k] = E[k] + W8^k O[k]
     C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
     C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
-    dft4<DIR>(e0, e1, e2, e3);
-    dft4<DIR>(o0, o1, o2, o3);
+    dft4<DIR, PK>(e0, e1, e2, e3);
+    dft4<DIR, PK>(o0, o1, o2, o3);
     o1 = w16<DIR, 2>(o1);
     o2 = w16<DIR, 4>(o2);
     o3 = w16<DIR, 6>(o3);
-    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
-    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
-    v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
-    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+    v[0] = kadd<PK>(e0, o0); v[4] = ksub<PK>(e0, o0);
+    v[1] = kadd<PK>(e1, o1); v[5] = ksub<PK>(e1, o1);
+    v[2] = kadd<PK>(e2, o2); v[6] = ksub<PK>(e2, o2);
+    v[3] = kadd<PK>(e3, o3); v[7] = ksub<PK>(e3, o3);
 }
 
-template <int DIR, typename C> __device__ __forceinline__ void dft16(C* v) {
+template <int DIR, bool PK = true, typename C> __device__ __forceinline__ void dft16(C* v) {
     // r = r1 + 4 r2, k = k1 + 4 k2:  A[r1][k1] = DFT4_r2(v[r1 + 4 r2]) W16^{r1 k1},
     // X[k1 + 4 k2] = DFT4_r1(A[r1][k1])
-    dft4<DIR>(v[0], v[4], v[8], v[12]);
-    dft4<DIR>(v[1], v[5], v[9], v[13]);
-    dft4<DIR>(v[2], v[6], v[10], v[14]);
-    dft4<DIR>(v[3], v[7], v[11], v[15]);
+    dft4<DIR, PK>(v[0], v[4], v[8], v[12]);
+    dft4<DIR, PK>(v[1], v[5], v[9], v[13]);
+    dft4<DIR, PK>(v[2], v[6], v[10], v[14]);
+    dft4<DIR, PK>(v[3], v[7], v[11], v[15]);
     // A[r1][k1] now sits at v[r1 + 4 k1]
     v[5] = w16<DIR, 1>(v[5]);   v[9] = w16<DIR, 2>(v[9]);   v[13] = w16<DIR, 3>(v[13]);
     v[6] = w16<DIR, 2>(v[6]);   v[10] = w16<DIR, 4>(v[10]); v[14] = w16<DIR, 6>(v[14]);
     v[7] = w16<DIR, 3>(v[7]);   v[11] = w16<DIR, 6>(v[11]); v[15] = w16<DIR, 9>(v[15]);
-    dft4<DIR>(v[0], v[1], v[2], v[3]);
-    dft4<DIR>(v[4], v[5], v[6], v[7]);
-    dft4<DIR>(v[8], v[9], v[10], v[11]);
-    dft4<DIR>(v[12], v[13], v[14], v[15]);
+    dft4<DIR, PK>(v[0], v[1], v[2], v[3]);
+    dft4<DIR, PK>(v[4], v[5], v[6], v[7]);
+    dft4<DIR, PK>(v[8], v[9], v[10], v[11]);
+    dft4<DIR, PK>(v[12], v[13], v[14], v[15]);
     // X[k1 + 4 k2] sits at v[4 k1 + k2]: transpose the 4x4 index
     C t;
     t = v[1]; v[1] = v[4]; v[4] = t;
@@ -168,14 +183,14 @@ template <int DIR, typename C> __device__ __forceinline__ void dft7(C* v) {
     }
 }
 
-template <int R, int DIR, typename C> __device__ __forceinline__ void dft_small(C* v) {
-    if constexpr (R == 2) dft2<DIR>(v[0], v[1]);
+template <int R, int DIR, bool PK = true, typename C> __device__ __forceinline__ void dft_small(C* v) {
+    if constexpr (R == 2) dft2<DIR, PK>(v[0], v[1]);
     else if constexpr (R == 3) dft3<DIR>(v);
-    else if constexpr (R == 4) dft4<DIR>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 4) dft4<DIR, PK>(v[0], v[1], v[2], v[3]);
     else if constexpr (R == 5) dft5<DIR>(v);
     else if constexpr (R == 7) dft7<DIR>(v);
-    else if constexpr (R == 8) dft8<DIR>(v);
-    else if constexpr (R == 16) dft16<DIR>(v);
+    else if constexpr (R == 8) dft8<DIR, PK>(v);
+    else if constexpr (R == 16) dft16<DIR, PK>(v);
 }
 
 // ---------------------------------------------------------------------------------

@@ -42,7 +42,7 @@ template <int N> __device__ __forceinline__ int p2_out_pos(int t, int idx) {
 // FA: exchange addresses as one base per butterfly plus compile-time offsets (fewer integer
 // instructions); !FA recomputes each padded index (fewer live registers, which the kernels
 // that hold a second set of 16 values need to stay within 128)
-template <int N, int DIR, int W, int S, bool FA, typename C>
+template <int N, int DIR, int W, int S, bool FA, bool PK, typename C>
 __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restrict__ tw, C (&v)[16]) {
     using P = Pow2<N>;
     constexpr int Rp = P::radix(S - 1);
@@ -112,8 +112,8 @@ __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restri
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < B; ++u) dft_small<R, DIR>(v + u * R);
-    if constexpr (S + 1 < P::NST) p2_stages<N, DIR, W, S + 1, FA>(c, t, sm, tw, v);
+    for (int u = 0; u < B; ++u) dft_small<R, DIR, PK>(v + u * R);
+    if constexpr (S + 1 < P::NST) p2_stages<N, DIR, W, S + 1, FA, PK>(c, t, sm, tw, v);
 }
 
 // Twiddle table of a length-N transform (built on the host): tw[e] = exp(-2 pi i e / N) for
@@ -122,13 +122,13 @@ __device__ __forceinline__ void p2_stages(int c, int t, C* sm, const C* __restri
 // ranges [N + Ns, N + 2 Ns) are disjoint and end below 2 N.
 // Full transform: v receives the outputs (positions from p2_out_pos).  All threads of the
 // block must call it (it synchronises the block); `sm` holds Pow2<N>::SMEM * W elements.
-template <int N, int DIR, int W, bool FA = true, typename C, class Load>
+template <int N, int DIR, int W, bool FA = true, bool PK = true, typename C, class Load>
 __device__ __forceinline__ void fft_p2(int c, int t, C* sm, const C* __restrict__ tw, Load&& load, C (&v)[16]) {
     using P = Pow2<N>;
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = load(t + r * P::G);
-    dft16<DIR>(v);
-    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1, FA>(c, t, sm, tw, v);
+    dft16<DIR, PK>(v);
+    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1, FA, PK>(c, t, sm, tw, v);
 }
 
 // Register m of thread t holds element t + G m: the order stage 0 reads its inputs in.  The
@@ -140,11 +140,11 @@ template <int N> __host__ __device__ constexpr int p2_out_m(int idx) {
 }
 
 // Full transform of the 16 values already in registers (v[m] = element t + G m).
-template <int N, int DIR, int W, bool FA = true, typename C>
+template <int N, int DIR, int W, bool FA = true, bool PK = true, typename C>
 __device__ __forceinline__ void fft_p2_regs(int c, int t, C* sm, const C* __restrict__ tw, C (&v)[16]) {
     using P = Pow2<N>;
-    dft16<DIR>(v);
-    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1, FA>(c, t, sm, tw, v);
+    dft16<DIR, PK>(v);
+    if constexpr (P::NST > 1) p2_stages<N, DIR, W, 1, FA, PK>(c, t, sm, tw, v);
 }
 
 }  // namespace dgt
