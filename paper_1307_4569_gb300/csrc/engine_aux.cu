@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(kThreadsBig) fir_synthesis_kernel(const cplx<T
     const int64_t ov = fp.Lg > fp.a ? fp.Lg - fp.a : 0;
     const int64_t lstart = fp.a * n0 - fp.center;
     const int64_t LM = fp.lam2 * fp.M;
-    C* seamL = seams + (b * nchunks + chunk) * 2 * ov;
-    C* seamR = seamL + ov;
+    const int64_t soff = (b * nchunks + chunk) * 2 * ov;
+    C* seamL = f_real ? reinterpret_cast<C*>(reinterpret_cast<R*>(seams) + soff) : seams + soff;
     for (int64_t t = threadIdx.x; t < S; t += blockDim.x) {
         const int64_t l = posmod(lstart + t, fp.L);
         const int64_t km = l % fp.M;
@@ -172,9 +172,11 @@ __global__ void __launch_bounds__(kThreadsBig) fir_synthesis_kernel(const cplx<T
             if (wn) v = cmul(v, fp.cisLM((int64_t)mulmod((uint64_t)(l % LM), (uint64_t)wn, (uint64_t)LM)));
             acc = cadd(acc, v);
         }
-        if (t < ov) seamL[t] = acc;
-        else if (t >= S - ov) seamR[t - (S - ov)] = acc;
-        else {
+        if (t < ov || t >= S - ov) {
+            const int64_t si = t < ov ? t : ov + t - (S - ov);      // seams of a real output are stored real
+            if (f_real) reinterpret_cast<R*>(seamL)[si] = acc.x;
+            else seamL[si] = acc;
+        } else {
             if (f_real) reinterpret_cast<R*>(f)[b * fp.L + l] = acc.x;
             else reinterpret_cast<C*>(f)[b * fp.L + l] = acc;
         }
@@ -192,12 +194,14 @@ __global__ void fir_seams_kernel(const cplx<T>* __restrict__ seams, void* __rest
         const int64_t chunk = (e / ov) % nchunks;
         const int64_t b = e / (ov * nchunks);
         const int64_t nxt = (chunk + 1) % nchunks;
-        const C r = seams[(b * nchunks + chunk) * 2 * ov + ov + t];
-        const C lft = seams[(b * nchunks + nxt) * 2 * ov + t];
+        const int64_t ir = (b * nchunks + chunk) * 2 * ov + ov + t, il = (b * nchunks + nxt) * 2 * ov + t;
         const int64_t l = posmod(fp.a * (chunk + 1) * fp.cols - fp.center + t, fp.L);
-        const C v = cadd(r, lft);
-        if (f_real) reinterpret_cast<T*>(f)[b * fp.L + l] = v.x;
-        else reinterpret_cast<C*>(f)[b * fp.L + l] = v;
+        if (f_real) {                                       // real seams for a real output
+            const T* sr = reinterpret_cast<const T*>(seams);
+            reinterpret_cast<T*>(f)[b * fp.L + l] = sr[ir] + sr[il];
+        } else {
+            reinterpret_cast<C*>(f)[b * fp.L + l] = cadd(seams[ir], seams[il]);
+        }
     }
 }
 

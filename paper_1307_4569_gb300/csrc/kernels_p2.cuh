@@ -42,6 +42,16 @@ template <typename T, int N> struct AdjCfg {
     static constexpr int MINB = HALVE ? 2 : 1;
 };
 
+// FIR analysis: CTAs of 128 threads (two rows for M = 1024), so that a dozen CTAs of 64-register
+// threads share an SM and the staging of one overlaps the transforms of the others (1.87 -> 1.73
+// ms against 256-thread CTAs on 64 audio signals)
+template <int N> struct AnaCfg {
+    static constexpr int G = N / 16;
+    static constexpr int RPB = G >= 128 ? 1 : 128 / G;
+    static constexpr int THREADS = RPB * G;
+    static constexpr int MINB = 65536 / (THREADS * 64) > 0 ? 65536 / (THREADS * 64) : 1;
+};
+
 template <int N> struct RowCfg {
     static constexpr int G = N / 16;
     static constexpr int RPB = G >= 256 ? 1 : 256 / G;                   // rows per CTA
@@ -408,11 +418,11 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
 // MULTI: windows longer than N (several taps per bin).  Float with Lg <= N is held to 64
 // registers, the occupancy of the other row kernels.
 template <typename T, int N, bool MULTI, bool SEG>
-__global__ void __launch_bounds__(RowCfg<N>::THREADS, sizeof(T) == 4 && !MULTI ? RowCfg<N>::MINB : 1)
+__global__ void __launch_bounds__(AnaCfg<N>::THREADS, sizeof(T) == 4 && !MULTI ? AnaCfg<N>::MINB : 1)
     fir_analysis_p2(const void* __restrict__ f, int f_real, cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
                     int64_t rows_total, const cplx<T>* __restrict__ tw) {
     using C = cplx<T>;
-    using RC = RowCfg<N>;
+    using RC = AnaCfg<N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gi = threadIdx.x / RC::G, t = threadIdx.x % RC::G;
     C* sm = reinterpret_cast<C*>(smem_raw) + gi * Pow2<N>::SMEM;
@@ -519,7 +529,8 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS, sizeof(T) == 4 && !MULTI ?
 // the real part only.  The first and last Lg - a samples of the segment, shared with the
 // neighbouring chunks, go to the seam buffer (fir_seams sums them); Lg <= M (one tap per bin).
 // RPB columns are transformed at once (RPB groups of N/16 threads): the largest count for 512
-// threads, or a quarter of it where the wider tiles of a larger element do not fit otherwise
+// threads, or a quarter of it (float chunks of 16+ columns in ~32 KB, and wherever the wider
+// tiles of a larger element do not fit otherwise)
 template <int N, int DIV = 1> struct SynCfg {
     static constexpr int G = N / 16;
     static constexpr int RPB0 = G >= 512 ? 1 : 512 / G;
@@ -598,18 +609,16 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_p2(cons
     const int ov = Lg > a ? Lg - a : 0;
     int64_t lstart = fp.a * n0 - fp.center;
     if (lstart < 0) lstart += fp.L;
-    C* seamL = seams + (b * nchunks + chunk) * 2 * ov;
-    C* seamR = seamL + ov;
+    // seams of a real output are stored real
+    A* seamL = reinterpret_cast<A*>(seams) + (b * nchunks + chunk) * 2 * ov;
+    A* seamR = seamL + ov;
     for (int tt = threadIdx.x; tt < S; tt += RC::THREADS) {
         int64_t l = lstart + tt;
         if (l >= fp.L) l -= fp.L;
-        C val;
-        if constexpr (REAL) val = mk(acc[tt], (T)0);
-        else val = acc[tt];
+        const A val = acc[tt];
         if (tt < ov) seamL[tt] = val;
         else if (tt >= S - ov) seamR[tt - (S - ov)] = val;
-        else if constexpr (REAL) reinterpret_cast<T*>(f)[b * fp.L + l] = val.x;
-        else reinterpret_cast<C*>(f)[b * fp.L + l] = val;
+        else reinterpret_cast<A*>(f)[b * fp.L + l] = val;
     }
 }
 
@@ -728,7 +737,7 @@ cudaError_t p2_pre_ifft_n(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_
 template <typename T, int N>
 cudaError_t p2_fir_analysis_n(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp, const void* tw,
                               int64_t B, cudaStream_t st) {
-    using RC = RowCfg<N>;
+    using RC = AnaCfg<N>;
     size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
     // staged segment: every CTA's columns in one signal, the segment shorter than the signal
     const int64_t S = (RC::RPB - 1) * fp.a + fp.Lg;
@@ -759,6 +768,15 @@ template <typename T, int N, int DIV> bool p2_fir_synthesis_fits(int64_t cols, i
            p2_fir_synthesis_smem<T, N, DIV>(cols, a, Lg, 0) <= kSmemBudget;
 }
 
+// float: quarter-width CTAs on chunks of at least 16 columns whose tile (real output) takes at
+// most 32 KB, about seven CTAs per SM (1.93 ms with half-width, 1.85 ms with quarter-width CTAs
+// against 2.08 ms with the full 512-thread CTAs and 64-column chunks, 64 audio signals; chunks
+// of 16 columns write 11 % more seam bytes than the coefficients they read)
+template <typename T, int N> bool p2_fir_synthesis_small(int64_t cols, int64_t Nn, int64_t a, int64_t Lg) {
+    return sizeof(T) == 4 && cols >= 16 && p2_fir_synthesis_fits<T, N, 4>(cols, Nn, a, Lg) &&
+           p2_fir_synthesis_smem<T, N, 4>(cols, a, Lg, 1) <= 32 * 1024;
+}
+
 template <typename T, int N, int DIV>
 cudaError_t p2_fir_synthesis_launch(const cplx<T>* c, void* f, int f_real, cplx<T>* seams,
                                     const FirParams<cplx<T>>& fp, const void* tw, int64_t B, cudaStream_t st) {
@@ -774,6 +792,8 @@ cudaError_t p2_fir_synthesis_launch(const cplx<T>* c, void* f, int f_real, cplx<
 template <typename T, int N>
 cudaError_t p2_fir_synthesis_n(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
                                const void* tw, int64_t B, cudaStream_t st) {
+    if (p2_fir_synthesis_small<T, N>(fp.cols, fp.N, fp.a, fp.Lg))
+        return p2_fir_synthesis_launch<T, N, 4>(c, f, f_real, seams, fp, tw, B, st);
     if (p2_fir_synthesis_fits<T, N, 1>(fp.cols, fp.N, fp.a, fp.Lg))
         return p2_fir_synthesis_launch<T, N, 1>(c, f, f_real, seams, fp, tw, B, st);
     if (p2_fir_synthesis_fits<T, N, 4>(fp.cols, fp.N, fp.a, fp.Lg))
@@ -788,6 +808,9 @@ template <typename T, int N> int64_t p2_fir_synthesis_cols_n(int64_t Nn, int64_t
     if (Lg > N) return 0;
     const int64_t D = (Lg + a - 1) / a;
     int64_t best = 0;
+    for (int64_t cols = D; cols <= 256; cols += D)
+        if (p2_fir_synthesis_small<T, N>(cols, Nn, a, Lg)) best = cols;
+    if (best) return best;
     for (int64_t cols = D; cols <= 256; cols += D)
         if (p2_fir_synthesis_fits<T, N, 1>(cols, Nn, a, Lg)) best = cols;
     if (best) return best;
