@@ -224,12 +224,22 @@ int dgt_logmag_loss(dgt_plan_t plan, const void* c, void* G, double* loss_dev, d
 int dgt_plan_bytes(dgt_plan_t plan, size_t* bytes);
 
 /* Synchronise `stream` and report a pending asynchronous CUDA error of this plan's work
- * as DGT_ERR_CUDA.  (No kernel of this library waits on another one; DGT_ERR_TIMEOUT is
- * reserved for bounded device waits.) */
+ * as DGT_ERR_CUDA, or DGT_ERR_TIMEOUT when a bounded device wait expired since the last
+ * check.  (No kernel of this library waits on another one.  The one device wait is the
+ * float synthesis kernel's wait for the tile copies it issued itself: a CTA whose wait
+ * exceeds the limit of dgt_wait_limit lets its copies land, records the expiry and returns,
+ * leaving its part of the output unwritten; the context stays usable.) */
 int dgt_plan_status(dgt_plan_t plan, void* stream);
 
-/* Synchronise `stream` and report a pending asynchronous CUDA error as DGT_ERR_CUDA. */
+/* Synchronise `stream` and report a pending asynchronous CUDA error as DGT_ERR_CUDA, or an
+ * expired bounded wait as DGT_ERR_TIMEOUT (as dgt_plan_status). */
 int dgt_sync(void* stream);
+
+/* Test hook: the limit, in SM clock cycles, of the bounded device waits of later launches
+ * (default 2e9, about a second).  cycles = 0 makes every wait expire at once, so that the
+ * error path can be tested without a fault; cycles < 0 only queries.  Returns the previous
+ * limit.  Host-global: it applies to every plan of the process. */
+long long dgt_wait_limit(long long cycles);
 
 /* Release the plan and its device memory (synchronises the device first). */
 void dgt_plan_destroy(dgt_plan_t plan);

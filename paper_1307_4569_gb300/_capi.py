@@ -71,6 +71,7 @@ SIGNATURES = {
     "dgt_plan_bytes": (i32, [vp, C.POINTER(C.c_size_t)]),
     "dgt_sync": (i32, [vp]),
     "dgt_plan_status": (i32, [vp, vp]),
+    "dgt_wait_limit": (C.c_longlong, [C.c_longlong]),
     "dgt_plan_destroy": (None, [vp]),
     "dgt_strerror": (C.c_char_p, [i32]),
     "dgt_last_error": (C.c_char_p, []),

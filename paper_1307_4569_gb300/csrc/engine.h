@@ -206,6 +206,12 @@ cudaError_t p2_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx
 template <typename T>
 cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
                        const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
+// Bounded device waits (the tensor-copy staging of fft_prod_adj): the wait limit in clock
+// cycles that launches pass to the kernels (a test hook lowers it), and the number of CTAs
+// whose wait expired since the last call (read and reset; synchronises the device).
+constexpr long long kWaitCycles = 2000000000LL;       // about a second
+extern long long g_wait_limit_cycles;
+int p2_take_wait_timeouts();
 // columns per chunk of the power-of-two FIR synthesis for FFT length M (0: not applicable)
 template <typename T> int64_t p2_fir_synthesis_cols(int64_t M, int64_t N, int64_t a, int64_t Lg);
 // lengths of the power-of-two column kernels

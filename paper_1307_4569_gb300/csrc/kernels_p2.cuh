@@ -11,6 +11,7 @@
 
 #include "fft_p2.cuh"
 #include "kcommon.cuh"
+#include "tma.cuh"
 
 namespace dgt {
 
@@ -176,6 +177,99 @@ __global__ void __launch_bounds__(AdjCfg<T, N>::THREADS, AdjCfg<T, N>::MINB) fft
             }
             __syncthreads();          // the next transform reuses the exchange buffer
         }
+    }
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) zf[b * g.L + (int64_t)p2_out_pos<N>(t, i) * g.K0 + k] = acc[i];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// fft_prod_adj, float, with the column tiles of Y staged by the tensor memory accelerator:
+// one thread issues the tile of the next (j, w) (d rows of W columns, in boxes of up to 256
+// rows) into the other of two shared buffers while the CTA transforms the current one, so the
+// transforms read shared memory instead of waiting on strided global loads.  Waits are bounded
+// (wait_limit cycles; 0 lets every wait expire at once, for tests); a CTA whose wait expires
+// lets its copies land, counts itself in g_tma_wait_timeouts and returns (the host reports
+// DGT_ERR_TIMEOUT).
+// ------------------------------------------------------------------------------------
+namespace {
+__device__ unsigned int g_tma_wait_timeouts = 0;
+}
+
+template <int N>
+__global__ void __launch_bounds__(AdjCfg<float, N>::THREADS, AdjCfg<float, N>::MINB)
+    fft_prod_adj_tma_p2(const __grid_constant__ CUtensorMap ymap, const float2* __restrict__ zg,
+                        float2* __restrict__ zf, SepGeom g, int64_t J, const float2* __restrict__ tw,
+                        long long wait_limit) {
+    using C = float2;
+    using CF = AdjCfg<float, N>;
+    constexpr int W = CF::W;
+    constexpr int BOXR = N < 256 ? N : 256;
+    constexpr int NB = N / BOXR;
+    constexpr uint32_t STAGE = (uint32_t)(N * W * sizeof(C));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C* stage = reinterpret_cast<C*>(smem_raw);
+    C* sm = reinterpret_cast<C*>(smem_raw + 2 * STAGE);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * STAGE + CF::SMEM);
+    const int c = threadIdx.x % W, t = threadIdx.x / W;
+    const int64_t b = blockIdx.y;
+    const int k0 = blockIdx.x * W;
+    const int64_t k = k0 + c;
+    const bool ok = k < g.M;
+    const int q = (int)g.q;
+    const int iters = (int)J * q;
+    const float scale = 1.f / (float)N;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // tile of iteration it = (j, w): rows w + q nu of Y[b][j], columns k0 .. k0 + W - 1
+    auto issue = [&](int it) {
+        const int j = it / q, w = it % q, s = it & 1;
+        mbar_arrive_expect_tx(bar + s, STAGE);
+        for (int i = 0; i < NB; ++i)
+            tma_load_3d(stage + (size_t)s * N * W + (size_t)i * BOXR * W, &ymap, k0, w,
+                        (int)((b * J + j) * N) + i * BOXR, bar + s);
+    };
+    if (threadIdx.x == 0) issue(0);
+    C acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = mk(0.f, 0.f);
+    for (int it = 0; it < iters; ++it) {
+        const int s = it & 1;
+        // buffer s ^ 1 was last read in iteration it - 1, before that iteration's final barrier
+        if (threadIdx.x == 0 && it + 1 < iters) issue(it + 1);
+        const bool late = wait_limit == 0 || !mbar_wait(bar + s, (uint32_t)((it >> 1) & 1), wait_limit);
+        if (__syncthreads_or(late)) {
+            if (threadIdx.x == 0) {
+                atomicAdd(&g_tma_wait_timeouts, 1u);
+                // the copies in flight land before the CTA's shared memory is released
+                mbar_wait(bar + s, (uint32_t)((it >> 1) & 1), kWaitCycles);
+                if (it + 1 < iters) mbar_wait(bar + (s ^ 1), (uint32_t)(((it + 1) >> 1) & 1), kWaitCycles);
+            }
+            return;
+        }
+        const int j = it / q, w = it % q;
+        const C* tile = stage + (size_t)s * N * W;
+        C v[16];
+        fft_p2<N, -1, W, false>(c, t, sm, tw, [&](int nu) -> C { return tile[nu * W + c]; }, v);
+        int64_t colG = k - g.a * w;
+        const bool wrap = colG < 0;
+        if (wrap) colG += g.K0;
+        const C* zgj = zg + j * g.L + colG;
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int xi = p2_out_pos<N>(t, i);
+                C u = cmul(cscale(v[i], scale), zgj[(int64_t)xi * g.K0]);
+                if (wrap) u = cmul(u, __ldg(tw + xi));
+                acc[i] = cadd(acc[i], u);
+            }
+        }
+        __syncthreads();          // the exchange buffer and buffer s are reused
     }
     if (ok) {
 #pragma unroll
@@ -673,10 +767,64 @@ cudaError_t p2_prod_ifft_n(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver
+// library); null when the driver does not offer it
+using TensorMapEncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                          const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                          CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                          CUtensorMapFloatOOBfill);
+inline TensorMapEncodeTiled tensor_map_encoder() {
+    static const TensorMapEncodeTiled fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) !=
+                cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess)
+            return (TensorMapEncodeTiled) nullptr;
+        return (TensorMapEncodeTiled)p;
+    }();
+    return fn;
+}
+
+// Y (rows (b J + j) d q + w + q nu, M columns) as a rank-3 tensor of 8-byte elements:
+// (k, w, (b J + j) d + nu) with strides (8, 8 M, 8 q M) bytes.  cudaErrorNotSupported when the
+// geometry is outside what the tile copies take (odd M, coordinates past 2^31, no encoder).
+template <int N>
+cudaError_t p2_fft_prod_adj_tma(const float2* y, const float2* zg, int64_t J, float2* zf, const SepGeom& g,
+                                const void* tw, int64_t B, cudaStream_t st) {
+    using CF = AdjCfg<float, N>;
+    constexpr int W = CF::W;
+    constexpr int BOXR = N < 256 ? N : 256;
+    static_assert(W * sizeof(float2) % 16 == 0, "tile rows of whole 16-byte units");
+    const TensorMapEncodeTiled enc = tensor_map_encoder();
+    if (!enc || g.M % 2 || g.d != N || B * J * N >= ((int64_t)1 << 31) || (reinterpret_cast<uintptr_t>(y) & 15))
+        return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.M, (cuuint64_t)g.q, (cuuint64_t)(B * J * N)};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.M * 8, (cuuint64_t)g.q * g.M * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)W, 1, (cuuint32_t)BOXR};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(y), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorNotSupported;
+    auto k = fft_prod_adj_tma_p2<N>;
+    const size_t smem = 2 * (size_t)N * W * sizeof(float2) + CF::SMEM + 2 * sizeof(uint64_t);
+    cudaError_t e = p2_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.M + W - 1) / W), (unsigned)B);
+    k<<<grid, CF::THREADS, smem, st>>>(map, zg, zf, g, J, (const float2*)tw, g_wait_limit_cycles);
+    return cudaGetLastError();
+}
+
 template <typename T, int N>
 cudaError_t p2_fft_prod_adj_n(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
                               const void* tw, int64_t B, cudaStream_t st) {
     using CF = AdjCfg<T, N>;
+    if constexpr (sizeof(T) == 4 && CF::HALVE && CF::W >= 2) {
+        const cudaError_t e = p2_fft_prod_adj_tma<N>(y, zg, J, zf, g, tw, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     auto k = fft_prod_adj_p2<T, N>;
     const size_t smem = CF::SMEM;
     cudaError_t e = p2_smem(k, smem);

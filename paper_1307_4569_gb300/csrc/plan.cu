@@ -30,6 +30,10 @@ static int fail(int status, const char* fmt, ...) {
     return status;
 }
 
+namespace dgt {
+long long g_wait_limit_cycles = kWaitCycles;
+}
+
 #define CUDA_TRY(...)                                                                                 \
     do {                                                                                              \
         cudaError_t _e = (__VA_ARGS__);                                                                      \
@@ -826,6 +830,8 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     int status_check(cudaStream_t st) override {
         CUDA_TRY(cudaStreamSynchronize(st));
         CUDA_TRY(cudaGetLastError());
+        if (const int n = p2_take_wait_timeouts())
+            return fail(DGT_ERR_TIMEOUT, "%d CTAs gave up waiting for their tile copies", n);
         return DGT_OK;
     }
     // the power-of-two kernels read / write channels 0..M/2 directly: the FIR kernels, and
@@ -1433,7 +1439,15 @@ int dgt_plan_status(dgt_plan_t plan, void* stream) {
 int dgt_sync(void* stream) {
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     CUDA_TRY(cudaGetLastError());
+    if (const int n = p2_take_wait_timeouts())
+        return fail(DGT_ERR_TIMEOUT, "%d CTAs gave up waiting for their tile copies", n);
     return DGT_OK;
+}
+
+long long dgt_wait_limit(long long cycles) {
+    const long long old = g_wait_limit_cycles;
+    if (cycles >= 0) g_wait_limit_cycles = cycles;
+    return old;
 }
 
 void dgt_plan_destroy(dgt_plan_t plan) {
