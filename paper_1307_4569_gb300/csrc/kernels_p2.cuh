@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(AdjCfg<float, N>::THREADS, AdjCfg<float, N>::M
     constexpr int BOXR = N < 256 ? N : 256;
     constexpr int NB = N / BOXR;
     constexpr uint32_t STAGE = (uint32_t)(N * W * sizeof(C));
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stage = reinterpret_cast<C*>(smem_raw);
     C* sm = reinterpret_cast<C*>(smem_raw + 2 * STAGE);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * STAGE + CF::SMEM);
