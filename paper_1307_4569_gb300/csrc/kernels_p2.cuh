@@ -787,7 +787,9 @@ inline TensorMapEncodeTiled tensor_map_encoder() {
 }
 
 // Y (rows (b J + j) d q + w + q nu, M columns) as a rank-3 tensor of 8-byte elements:
-// (k, w, (b J + j) d + nu) with strides (8, 8 M, 8 q M) bytes.  cudaErrorNotSupported when the
+// (k, w, (b J + j) d + nu) with strides (8, 8 M, 8 q M) bytes; L2 fills of 128 bytes (1.90 ms
+// against 2.00 ms with 64-byte fills on 64 audio signals; full-width tiles of 8 columns with
+// one CTA per SM: 1.97 ms).  cudaErrorNotSupported when the
 // geometry is outside what the tile copies take (odd M, coordinates past 2^31, no encoder).
 template <int N>
 cudaError_t p2_fft_prod_adj_tma(const float2* y, const float2* zg, int64_t J, float2* zf, const SepGeom& g,
@@ -805,7 +807,7 @@ cudaError_t p2_fft_prod_adj_tma(const float2* y, const float2* zg, int64_t J, fl
     const cuuint32_t box[3] = {(cuuint32_t)W, 1, (cuuint32_t)BOXR};
     const cuuint32_t estr[3] = {1, 1, 1};
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(y), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorNotSupported;
     auto k = fft_prod_adj_tma_p2<N>;
