@@ -188,7 +188,10 @@ __global__ void __launch_bounds__(AdjCfg<T, N>::THREADS, AdjCfg<T, N>::MINB) fft
 // fft_prod_adj, float, with the column tiles of Y staged by the tensor memory accelerator:
 // one thread issues the tile of the next (j, w) (d rows of W columns, in boxes of up to 256
 // rows) into the other of two shared buffers while the CTA transforms the current one, so the
-// transforms read shared memory instead of waiting on strided global loads.  Waits are bounded
+// transforms read shared memory instead of waiting on strided global loads.  ZGT: the window
+// factor tile ZG~_j[.][k0 - a w ..] of the current (j, w) is copied the same way into the
+// buffer whose Y values have just been read, during the transform; the Y tile two iterations
+// ahead follows once the products are summed.  Waits are bounded
 // (wait_limit cycles; 0 lets every wait expire at once, for tests); a CTA whose wait expires
 // lets its copies land, counts itself in g_tma_wait_timeouts and returns (the host reports
 // DGT_ERR_TIMEOUT).
@@ -197,21 +200,23 @@ namespace {
 __device__ unsigned int g_tma_wait_timeouts = 0;
 }
 
-template <int N>
+template <int N, bool ZGT>
 __global__ void __launch_bounds__(AdjCfg<float, N>::THREADS, AdjCfg<float, N>::MINB)
-    fft_prod_adj_tma_p2(const __grid_constant__ CUtensorMap ymap, const float2* __restrict__ zg,
-                        float2* __restrict__ zf, SepGeom g, int64_t J, const float2* __restrict__ tw,
-                        long long wait_limit) {
+    fft_prod_adj_tma_p2(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap zgmap,
+                        const float2* __restrict__ zg, float2* __restrict__ zf, SepGeom g, int64_t J,
+                        const float2* __restrict__ tw, long long wait_limit) {
     using C = float2;
     using CF = AdjCfg<float, N>;
     constexpr int W = CF::W;
+    constexpr int G = Pow2<N>::G;
     constexpr int BOXR = N < 256 ? N : 256;
     constexpr int NB = N / BOXR;
     constexpr uint32_t STAGE = (uint32_t)(N * W * sizeof(C));
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stage = reinterpret_cast<C*>(smem_raw);
     C* sm = reinterpret_cast<C*>(smem_raw + 2 * STAGE);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * STAGE + CF::SMEM);
+    uint64_t* barY = reinterpret_cast<uint64_t*>(smem_raw + 2 * STAGE + CF::SMEM);
+    uint64_t* barZ = barY + 2;
     const int c = threadIdx.x % W, t = threadIdx.x / W;
     const int64_t b = blockIdx.y;
     const int k0 = blockIdx.x * W;
@@ -221,55 +226,111 @@ __global__ void __launch_bounds__(AdjCfg<float, N>::THREADS, AdjCfg<float, N>::M
     const int iters = (int)J * q;
     const float scale = 1.f / (float)N;
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
+        mbar_init(barY, 1);
+        mbar_init(barY + 1, 1);
+        mbar_init(barZ, 1);
+        mbar_init(barZ + 1, 1);
         mbar_fence_init();
     }
     __syncthreads();
-    // tile of iteration it = (j, w): rows w + q nu of Y[b][j], columns k0 .. k0 + W - 1
-    auto issue = [&](int it) {
+    // Y tile of iteration it = (j, w): rows w + q nu of Y[b][j], columns k0 .. k0 + W - 1
+    auto issue_y = [&](int it) {
         const int j = it / q, w = it % q, s = it & 1;
-        mbar_arrive_expect_tx(bar + s, STAGE);
+        mbar_arrive_expect_tx(barY + s, STAGE);
         for (int i = 0; i < NB; ++i)
             tma_load_3d(stage + (size_t)s * N * W + (size_t)i * BOXR * W, &ymap, k0, w,
-                        (int)((b * J + j) * N) + i * BOXR, bar + s);
+                        (int)((b * J + j) * N) + i * BOXR, barY + s);
     };
-    if (threadIdx.x == 0) issue(0);
+    // window factor tile of iteration it: rows xi of ZG~_j, columns k0 - a w (+ K0), into the
+    // buffer whose Y tile has just been read
+    auto issue_z = [&](int it) {
+        const int j = it / q, w = it % q, s = it & 1;
+        int64_t col0 = k0 - g.a * w;
+        if (col0 < 0) col0 += g.K0;
+        mbar_arrive_expect_tx(barZ + s, STAGE);
+        for (int i = 0; i < NB; ++i)
+            tma_load_3d(stage + (size_t)s * N * W + (size_t)i * BOXR * W, &zgmap, (int)col0, 0, j * N + i * BOXR,
+                        barZ + s);
+    };
+    // the copies of this CTA still in flight land before its shared memory is released
+    auto drain = [&](int it, bool y_now, bool z_now) {
+        const uint32_t ph = (uint32_t)((it >> 1) & 1);
+        if (y_now) mbar_wait(barY + (it & 1), ph, kWaitCycles);
+        if (z_now) mbar_wait(barZ + (it & 1), ph, kWaitCycles);
+        if (it + 1 < iters) mbar_wait(barY + ((it + 1) & 1), (uint32_t)(((it + 1) >> 1) & 1), kWaitCycles);
+    };
+    if (threadIdx.x == 0) {
+        issue_y(0);
+        if constexpr (ZGT) {
+            if (iters > 1) issue_y(1);
+        }
+    }
     C acc[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) acc[i] = mk(0.f, 0.f);
     for (int it = 0; it < iters; ++it) {
         const int s = it & 1;
-        // buffer s ^ 1 was last read in iteration it - 1, before that iteration's final barrier
-        if (threadIdx.x == 0 && it + 1 < iters) issue(it + 1);
-        const bool late = wait_limit == 0 || !mbar_wait(bar + s, (uint32_t)((it >> 1) & 1), wait_limit);
-        if (__syncthreads_or(late)) {
-            if (threadIdx.x == 0) {
-                atomicAdd(&g_tma_wait_timeouts, 1u);
-                // the copies in flight land before the CTA's shared memory is released
-                mbar_wait(bar + s, (uint32_t)((it >> 1) & 1), kWaitCycles);
-                if (it + 1 < iters) mbar_wait(bar + (s ^ 1), (uint32_t)(((it + 1) >> 1) & 1), kWaitCycles);
-            }
-            return;
-        }
+        const uint32_t ph = (uint32_t)((it >> 1) & 1);
         const int j = it / q, w = it % q;
         const C* tile = stage + (size_t)s * N * W;
         C v[16];
-        fft_p2<N, -1, W, false>(c, t, sm, tw, [&](int nu) -> C { return tile[nu * W + c]; }, v);
+        if constexpr (ZGT) {
+            const bool late = wait_limit == 0 || !mbar_wait(barY + s, ph, wait_limit);
+#pragma unroll
+            for (int m = 0; m < 16; ++m) v[m] = tile[(t + G * m) * W + c];
+            if (__syncthreads_or(late)) {         // also: every thread has read its Y values
+                if (threadIdx.x == 0) {
+                    atomicAdd(&g_tma_wait_timeouts, 1u);
+                    drain(it, true, false);
+                }
+                return;
+            }
+            if (threadIdx.x == 0) issue_z(it);
+            fft_p2_regs<N, -1, W, false>(c, t, sm, tw, v);
+        } else {
+            // buffer s ^ 1 was last read in iteration it - 1, before that iteration's final barrier
+            if (threadIdx.x == 0 && it + 1 < iters) issue_y(it + 1);
+            const bool late = wait_limit == 0 || !mbar_wait(barY + s, ph, wait_limit);
+            if (__syncthreads_or(late)) {
+                if (threadIdx.x == 0) {
+                    atomicAdd(&g_tma_wait_timeouts, 1u);
+                    drain(it, true, false);
+                }
+                return;
+            }
+            fft_p2<N, -1, W, false>(c, t, sm, tw, [&](int nu) -> C { return tile[nu * W + c]; }, v);
+        }
         int64_t colG = k - g.a * w;
         const bool wrap = colG < 0;
         if (wrap) colG += g.K0;
-        const C* zgj = zg + j * g.L + colG;
-        if (ok) {
+        bool lateZ = false;
+        if constexpr (ZGT) lateZ = wait_limit == 0 || !mbar_wait(barZ + s, ph, wait_limit);
+        if (ok && !lateZ) {
+            const C* zgj = zg + j * g.L + colG;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int xi = p2_out_pos<N>(t, i);
-                C u = cmul(cscale(v[i], scale), zgj[(int64_t)xi * g.K0]);
+                C zv;
+                if constexpr (ZGT) zv = tile[xi * W + c];
+                else zv = zgj[(int64_t)xi * g.K0];
+                C u = cmul(cscale(v[i], scale), zv);
                 if (wrap) u = cmul(u, __ldg(tw + xi));
                 acc[i] = cadd(acc[i], u);
             }
         }
-        __syncthreads();          // the exchange buffer and buffer s are reused
+        // the exchange buffer and buffer s are reused
+        if constexpr (ZGT) {
+            if (__syncthreads_or(lateZ)) {
+                if (threadIdx.x == 0) {
+                    atomicAdd(&g_tma_wait_timeouts, 1u);
+                    drain(it, false, true);
+                }
+                return;
+            }
+            if (threadIdx.x == 0 && it + 2 < iters) issue_y(it + 2);
+        } else {
+            __syncthreads();
+        }
     }
     if (ok) {
 #pragma unroll
@@ -801,21 +862,33 @@ cudaError_t p2_fft_prod_adj_tma(const float2* y, const float2* zg, int64_t J, fl
     const TensorMapEncodeTiled enc = tensor_map_encoder();
     if (!enc || g.M % 2 || g.d != N || B * J * N >= ((int64_t)1 << 31) || (reinterpret_cast<uintptr_t>(y) & 15))
         return cudaErrorNotSupported;
-    CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)g.M, (cuuint64_t)g.q, (cuuint64_t)(B * J * N)};
-    const cuuint64_t strides[2] = {(cuuint64_t)g.M * 8, (cuuint64_t)g.q * g.M * 8};
     const cuuint32_t box[3] = {(cuuint32_t)W, 1, (cuuint32_t)BOXR};
     const cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(y), dims, strides, box, estr,
+    CUtensorMap ymap, zgmap;
+    const cuuint64_t ydims[3] = {(cuuint64_t)g.M, (cuuint64_t)g.q, (cuuint64_t)(B * J * N)};
+    const cuuint64_t ystrides[2] = {(cuuint64_t)g.M * 8, (cuuint64_t)g.q * g.M * 8};
+    if (enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(y), ydims, ystrides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorNotSupported;
-    auto k = fft_prod_adj_tma_p2<N>;
-    const size_t smem = 2 * (size_t)N * W * sizeof(float2) + CF::SMEM + 2 * sizeof(uint64_t);
+    // the window factor tiles too when a tile never straddles the wrap (a % W == 0) and rows of
+    // ZG~ (K0 columns) start on 16-byte boundaries
+    bool zgt = g.a % W == 0 && g.K0 % 2 == 0 && g.L == g.d * g.K0 && J * N < ((int64_t)1 << 31) &&
+               !(reinterpret_cast<uintptr_t>(zg) & 15);
+    if (zgt) {
+        const cuuint64_t zdims[3] = {(cuuint64_t)g.K0, 1, (cuuint64_t)(J * N)};
+        const cuuint64_t zstrides[2] = {(cuuint64_t)g.K0 * 8, (cuuint64_t)g.K0 * 8};
+        zgt = enc(&zgmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(zg), zdims, zstrides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    if (!zgt) zgmap = ymap;                                 // not read
+    auto k = zgt ? fft_prod_adj_tma_p2<N, true> : fft_prod_adj_tma_p2<N, false>;
+    const size_t smem = 2 * (size_t)N * W * sizeof(float2) + CF::SMEM + 4 * sizeof(uint64_t);
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.M + W - 1) / W), (unsigned)B);
-    k<<<grid, CF::THREADS, smem, st>>>(map, zg, zf, g, J, (const float2*)tw, g_wait_limit_cycles);
+    k<<<grid, CF::THREADS, smem, st>>>(ymap, zgmap, zg, zf, g, J, (const float2*)tw, g_wait_limit_cycles);
     return cudaGetLastError();
 }
 
