@@ -693,7 +693,9 @@ template <int N, int DIV = 1> struct SynCfg {
     static constexpr int THREADS = RPB * G;
 };
 
-template <typename T, int N, bool REAL, int DIV>
+// MTS: the modulated taps (lam2 Lg values) are first copied to shared memory, after the
+// accumulator, and read from there in the scatter.
+template <typename T, int N, bool REAL, int DIV, bool MTS = false>
 __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_p2(const cplx<T>* __restrict__ c,
                                                                        void* __restrict__ f,
                                                                        cplx<T>* __restrict__ seams,
@@ -718,6 +720,13 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_p2(cons
     for (int i = threadIdx.x; i < S; i += RC::THREADS) {
         if constexpr (REAL) acc[i] = (T)0;
         else acc[i] = mk((T)0, (T)0);
+    }
+    const C* mtab = fp.mtaps;
+    if constexpr (MTS) {
+        C* smt = reinterpret_cast<C*>(
+            smem_raw + ((sizeof(C) * (size_t)Pow2<N>::SMEM * RC::RPB + sizeof(A) * (size_t)S + 15) & ~(size_t)15));
+        for (int i = threadIdx.x; i < (int)fp.lam2 * Lg; i += RC::THREADS) smt[i] = fp.mtaps[i];
+        mtab = smt;
     }
     __syncthreads();
     for (int q = 0; q < D; ++q) {
@@ -745,14 +754,16 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_p2(cons
                 if (ln < 0) ln += fp.L;
                 const int lnm = (int)(ln & (N - 1));
                 const C ph = wn ? fp.cisLM(ln * wn) : mk((T)1, (T)0);
-                const C* mt = fp.mtaps + (int64_t)wn * Lg;
+                const C* mt = mtab + (int64_t)wn * Lg;
                 A* ar = acc + r * a;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int tap = (p2_out_pos<N>(t, i) - lnm) & (N - 1);
                     if (tap < Lg) {
                         const C u = wn ? cmul(v[i], ph) : v[i];
-                        const C m = __ldg(mt + tap);
+                        C m;
+                        if constexpr (MTS) m = mt[tap];
+                        else m = __ldg(mt + tap);
                         if constexpr (REAL) ar[tap] += u.x * m.x + u.y * m.y;
                         else ar[tap] = cadd(ar[tap], cmulc(u, m));
                     }
@@ -1003,11 +1014,23 @@ template <typename T, int N> bool p2_fir_synthesis_small(int64_t cols, int64_t N
 template <typename T, int N, int DIV>
 cudaError_t p2_fir_synthesis_launch(const cplx<T>* c, void* f, int f_real, cplx<T>* seams,
                                     const FirParams<cplx<T>>& fp, const void* tw, int64_t B, cudaStream_t st) {
-    const size_t smem = p2_fir_synthesis_smem<T, N, DIV>(fp.cols, fp.a, fp.Lg, f_real);
+    size_t smem = p2_fir_synthesis_smem<T, N, DIV>(fp.cols, fp.a, fp.Lg, f_real);
+    dim3 grid((unsigned)(fp.N / fp.cols), (unsigned)B);
+    const size_t mtb = sizeof(cplx<T>) * (size_t)(fp.lam2 * fp.Lg);
+    if constexpr (sizeof(T) == 4 && DIV == 4) {
+        // float quarter-width CTAs: modulated taps from shared memory when they take <= 16 KB
+        if (mtb <= 16 * 1024) {
+            smem = ((smem + 15) & ~(size_t)15) + mtb;
+            auto k = f_real ? fir_synthesis_p2<T, N, true, DIV, true> : fir_synthesis_p2<T, N, false, DIV, true>;
+            cudaError_t e = p2_smem(k, smem);
+            if (e != cudaSuccess) return e;
+            k<<<grid, SynCfg<N, DIV>::THREADS, smem, st>>>(c, f, seams, fp, (const cplx<T>*)tw);
+            return cudaGetLastError();
+        }
+    }
     auto k = f_real ? fir_synthesis_p2<T, N, true, DIV> : fir_synthesis_p2<T, N, false, DIV>;
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(fp.N / fp.cols), (unsigned)B);
     k<<<grid, SynCfg<N, DIV>::THREADS, smem, st>>>(c, f, seams, fp, (const cplx<T>*)tw);
     return cudaGetLastError();
 }
