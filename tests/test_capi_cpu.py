@@ -39,3 +39,15 @@ def test_binding_loads_and_reports_errors(libpath):
 
 def test_build_is_incremental(libpath):
     assert B.up_to_date()
+
+
+def test_wait_limit_hook_sets_queries_and_restores(libpath):
+    # host-side state only: the limit later launches pass to their bounded waits
+    lib = K.lib()
+    default = lib.dgt_wait_limit(-1)
+    assert default == 2000000000
+    assert lib.dgt_wait_limit(12345) == default
+    assert lib.dgt_wait_limit(-1) == 12345
+    assert lib.dgt_wait_limit(0) == 12345
+    assert lib.dgt_wait_limit(default) == 0
+    assert lib.dgt_wait_limit(-1) == default
