@@ -106,15 +106,20 @@ def dgt_fold(f, g, a, M, lam1=0, lam2=1, cols=None) -> np.ndarray:
     return out
 
 
-def idgt_fold(c, gamma, a, M, lam1=0, lam2=1) -> np.ndarray:
-    """Adjoint of dgt_fold: unnormalised inverse FFT_M per column, unfold, window, sum."""
+def idgt_fold(c, gamma, a, M, lam1=0, lam2=1, cols=None) -> np.ndarray:
+    """Adjoint of dgt_fold: unnormalised inverse FFT_M per column, unfold, window, sum.
+
+    O(L) per time position.  ``cols`` lists the time positions n that ``c`` holds (shape
+    (M, len(cols))): the synthesis of a coefficient array that is zero on every other
+    column."""
     gamma = np.asarray(gamma, dtype=np.complex128)
     L = gamma.shape[0]
     lat = Lattice(L, a, M, lam1, lam2)
     l = np.arange(L, dtype=np.int64)
     f = np.zeros(L, dtype=np.complex128)
-    for n in range(lat.N):
-        h = np.fft.ifft(c[:, n]) * M
+    cols = list(range(lat.N)) if cols is None else list(cols)
+    for i, n in enumerate(cols):
+        h = np.fft.ifft(c[:, i]) * M
         mod = _cexp(l * lat.freq_offset_num(n), lam2 * M, sign=+1.0)
         f += np.tile(h, L // M) * gamma[(l - a * n) % L] * mod
     return f

@@ -178,6 +178,21 @@ def test_synthesis_matches_direct_small():
         assert np.linalg.norm(bw(cc, g, a, M, l1, l2) - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_synthesis_of_selected_columns_matches_direct():
+    """idgt_fold(cols=S) on the columns S equals the direct synthesis (Section 2.1, inversion
+    formula) of the full array that is zero outside S, for every lambda2 and column mix
+    (first, last, both parities of w(n))."""
+    for L, a, M, l1, l2 in ((48, 4, 8, 1, 2), (72, 6, 12, 1, 3), (64, 4, 16, 0, 1)):
+        N = L // a
+        g = _crand(L)
+        cols = [0, 1, N // 2 + 1, N - 1]
+        cc = np.zeros((M, N), dtype=np.complex128)
+        cc[:, cols] = RNG.standard_normal((M, len(cols))) + 1j * RNG.standard_normal((M, len(cols)))
+        ref = D.idgt_direct(cc, g, a, M, l1, l2)
+        got = D.idgt_fold(cc[:, cols], g, a, M, l1, l2, cols=cols)
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
 def test_pchirp_is_second_degree_character():
     """pchirp(L, s)(l + x) = pchirp(L, s)(l) pchirp(L, s)(x) e^{2 pi i s l x / L}: the
     identity used in Lemma meta_phases for U_{S_c}; with (L+1) it holds for odd and even L."""
