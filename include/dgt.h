@@ -22,7 +22,9 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is enqueued
  *     asynchronously; no entry point synchronises the stream unless stated.
  *   - Return value: DGT_OK or a dgt_status code; dgt_last_error() gives a message.
- *     Asynchronous device faults surface at the next call that synchronises.
+ *     Asynchronous device faults surface at the next call that synchronises.  An expired
+ *     bounded device wait of a plan's earlier synthesis (see dgt_plan_status) is returned as
+ *     DGT_ERR_TIMEOUT by that plan's next call, which then enqueues nothing.
  *   - A plan is not thread-safe: use one plan per host thread or serialise calls.
  */
 #ifndef DGT_H
@@ -158,6 +160,17 @@ int dgt_exec(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t bat
 int idgt_exec(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
               void* stream);
 
+/* Synthesis with a window of the caller's choosing (Section 2.1, inversion formula with an
+ * arbitrary synthesis window gamma: f(l) = sum_{m,n} c(m, n) gamma(l - a n)
+ * exp(+2 pi i l (m + w(n)) / M)).  gamma: DEVICE buffer of the plan's precision, real
+ * (gamma_is_real = 1) or interleaved complex; L samples for the coset and shear routes, or the
+ * plan's Lg taps (same centre as the analysis window) for the FIR route.  The window's
+ * factorisation is rebuilt on `stream` at every call (one transform of gamma, O(L log L);
+ * plan-owned memory, grown with cudaMalloc on first use), so the call may allocate.
+ * Errors: DGT_ERR_UNSUPPORTED for blockwise plans, and those of idgt_exec. */
+int idgt_exec_window(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, const void* gamma,
+                     int gamma_is_real, void* stream);
+
 /* Real-signal coefficients (the real-signal variant of the interface, Section 4.4): for a real
  * signal and a real window on a lattice with lambda2 <= 2 and M even,
  * c(m, n) = conj(c((-m - 2 w(n)) mod M, n)), so the channels 0..M/2 determine c.
@@ -175,7 +188,11 @@ int dgt_workspace_bytes(dgt_plan_t plan, int64_t batch, size_t* bytes);
 
 /* As dgt_exec / idgt_exec, with a caller-provided device workspace of at least
  * dgt_workspace_bytes(batch) bytes, 256-byte aligned.  These never allocate (the dual /
- * tight window of idgt_exec_ws must already be cached by dgt_window_dual / _tight). */
+ * tight window of idgt_exec_ws must already be cached by dgt_window_dual / _tight).
+ * The first word of the workspace is the call's expiry word: idgt_exec_ws clears it in
+ * stream order before its kernels, and a kernel whose bounded wait expires sets it;
+ * dgt_workspace_status reads it.  Calls on different streams with different workspaces
+ * may run concurrently; calls sharing a workspace must be ordered. */
 int dgt_exec_ws(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* workspace,
                 void* stream);
 int idgt_exec_ws(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
@@ -224,16 +241,24 @@ int dgt_logmag_loss(dgt_plan_t plan, const void* c, void* G, double* loss_dev, d
 int dgt_plan_bytes(dgt_plan_t plan, size_t* bytes);
 
 /* Synchronise `stream` and report a pending asynchronous CUDA error of this plan's work
- * as DGT_ERR_CUDA, or DGT_ERR_TIMEOUT when a bounded device wait expired since the last
- * check.  (No kernel of this library waits on another one.  The one device wait is the
+ * as DGT_ERR_CUDA, or DGT_ERR_TIMEOUT when a bounded device wait of this plan's calls
+ * without a caller workspace expired since the last check (each plan has its own expiry
+ * word; dgt_workspace_status covers the calls with a caller workspace).  (No kernel of this library waits on another one.  The one device wait is the
  * float synthesis kernel's wait for the tile copies it issued itself: a CTA whose wait
  * exceeds the limit of dgt_wait_limit lets its copies land, records the expiry and returns,
  * leaving its part of the output unwritten; the context stays usable.) */
 int dgt_plan_status(dgt_plan_t plan, void* stream);
 
 /* Synchronise `stream` and report a pending asynchronous CUDA error as DGT_ERR_CUDA, or an
- * expired bounded wait as DGT_ERR_TIMEOUT (as dgt_plan_status). */
+ * expired bounded wait of any live plan's calls without a caller workspace as
+ * DGT_ERR_TIMEOUT (clearing those plans' words). */
 int dgt_sync(void* stream);
+
+/* Synchronise `stream` (the one the idgt_exec_ws call ran on) and report DGT_ERR_TIMEOUT when
+ * a kernel of the last synthesis that used `workspace` gave up waiting for its tile copies
+ * (its output is then incomplete), clearing the word; DGT_ERR_CUDA for a pending CUDA
+ * error.  A serving loop calls it per batch to attribute an expiry to that batch. */
+int dgt_workspace_status(dgt_plan_t plan, const void* workspace, void* stream);
 
 /* Test hook: the limit, in SM clock cycles, of the bounded device waits of later launches
  * (default 2e9, about a second).  cycles = 0 makes every wait expire at once, so that the

@@ -27,13 +27,14 @@ def loss(f, g, a, M, lam1, lam2, eps=1e-6) -> float:
     return float(np.sum(np.log(np.abs(c) ** 2 + eps)))
 
 
-def grads(f, g, a, M, lam1, lam2, eps=1e-6):
-    """Return (loss, grad_f, grad_g) for one signal."""
+def grads(f, g, a, M, lam1, lam2, eps=1e-6, coefs=None):
+    """Return (loss, grad_f, grad_g) for one signal.  ``coefs`` (shape (M, N)) stands in for
+    c = C_g f in every later step (to measure how the gradients respond to an error in c)."""
     f = np.asarray(f)
     g = np.asarray(g)
     L = f.shape[0]
     lat = Lattice(L, a, M, lam1, lam2)
-    c = dgt_fold(f, g, a, M, lam1, lam2)
+    c = dgt_fold(f, g, a, M, lam1, lam2) if coefs is None else np.asarray(coefs, dtype=np.complex128)
     u = c / (np.abs(c) ** 2 + eps)
     lval = float(np.sum(np.log(np.abs(c) ** 2 + eps)))
     v = idgt_fold(u, g, a, M, lam1, lam2)

@@ -60,6 +60,7 @@ SIGNATURES = {
     "dgt_exec_real": (i32, [vp, vp, vp, i64, vp]),
     "idgt_exec_real": (i32, [vp, vp, vp, i64, i32, vp]),
     "idgt_exec": (i32, [vp, vp, vp, i32, i64, i32, vp]),
+    "idgt_exec_window": (i32, [vp, vp, vp, i32, i64, vp, i32, vp]),
     "dgt_workspace_bytes": (i32, [vp, i64, C.POINTER(C.c_size_t)]),
     "dgt_exec_ws": (i32, [vp, vp, i32, vp, i64, vp, vp]),
     "idgt_exec_ws": (i32, [vp, vp, vp, i32, i64, i32, vp, vp]),
@@ -71,6 +72,7 @@ SIGNATURES = {
     "dgt_plan_bytes": (i32, [vp, C.POINTER(C.c_size_t)]),
     "dgt_sync": (i32, [vp]),
     "dgt_plan_status": (i32, [vp, vp]),
+    "dgt_workspace_status": (i32, [vp, vp, vp]),
     "dgt_wait_limit": (C.c_longlong, [C.c_longlong]),
     "dgt_plan_destroy": (None, [vp]),
     "dgt_strerror": (C.c_char_p, [i32]),

@@ -113,6 +113,26 @@ class Plan:
                                   _stream(stream)))
         return out
 
+    def idgt_window(self, c: torch.Tensor, gamma: torch.Tensor, real: bool = False, out=None, stream=None):
+        """Synthesis with the caller's window gamma (CUDA tensor of the plan precision, real or
+        complex; L samples, or the FIR taps for an FIR-route plan)."""
+        if not c.is_cuda or not c.is_contiguous() or c.dtype != self.cdtype:
+            raise TypeError("coefficients must be a contiguous CUDA %s tensor" % self.cdtype)
+        if tuple(c.shape[-2:]) != (self.N, self.M):
+            raise ValueError("coefficient shape %s != (N, M)=(%d, %d)" % (tuple(c.shape), self.N, self.M))
+        if not gamma.is_cuda or not gamma.is_contiguous() or gamma.dtype not in (self.rdtype, self.cdtype):
+            raise TypeError("window must be a contiguous CUDA tensor of the plan precision")
+        want = self.info["fir_len"] if self.info["route_name"] == "fir" else self.L
+        if gamma.numel() != want:
+            raise ValueError("window length %d != %d" % (gamma.numel(), want))
+        B = int(np.prod(c.shape[:-2])) if c.dim() > 2 else 1
+        if out is None:
+            out = torch.empty(tuple(c.shape[:-2]) + (self.L,), dtype=self.rdtype if real else self.cdtype,
+                              device=c.device)
+        K.check(K.lib().idgt_exec_window(self._h, c.data_ptr(), out.data_ptr(), int(real), B, gamma.data_ptr(),
+                                         int(not gamma.is_complex()), _stream(stream)))
+        return out
+
     def dgtreal(self, f: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Channels 0..M/2 of the coefficients of real signals f[..., L] (real window,
         lambda2 <= 2, M even): c[..., n, m], m <= M/2."""
@@ -188,8 +208,14 @@ class Plan:
         return out
 
     def status(self, stream=None) -> None:
-        """Synchronise and raise DGTError(DGT_ERR_TIMEOUT) if a bounded device wait expired."""
+        """Synchronise and raise DGTError(DGT_ERR_TIMEOUT) if a bounded device wait of this
+        plan's calls without a caller workspace expired (the plan's next call raises it too)."""
         K.check(K.lib().dgt_plan_status(self._h, _stream(stream)))
+
+    def workspace_status(self, workspace: torch.Tensor, stream=None) -> None:
+        """Synchronise `stream` and raise DGTError(DGT_ERR_TIMEOUT) if the last synthesis that
+        used `workspace` (idgt_ws) had a kernel give up waiting for its tile copies."""
+        K.check(K.lib().dgt_workspace_status(self._h, workspace.data_ptr(), _stream(stream)))
 
     def plan_bytes(self) -> int:
         v = C.c_size_t()

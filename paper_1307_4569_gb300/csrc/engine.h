@@ -88,7 +88,7 @@ cudaError_t launch_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int6
 
 template <typename T>
 cudaError_t launch_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
-                                const FftRef& fd, int64_t B, cudaStream_t st);
+                                const FftRef& fd, int64_t B, unsigned int* expired, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_zak_inv(const cplx<T>* zf, int64_t zf_bstride, void* dst, int dst_real, int64_t dst_bstride,
@@ -124,6 +124,8 @@ template <typename C> struct FirParams {
     int64_t cols;                     // time positions per CTA
     int64_t group;                    // rows transformed at once (spare buffer rows)
     int half;                         // coefficients hold channels 0..M/2 only (real signals, lam2 <= 2)
+    int pairable;                     // the window of these taps is real: real-input pairing applies
+    const C* hb;                      // exp(-pi i k / M), k < M (lam2 = 2; real-input pairing)
 };
 template <typename T>
 cudaError_t launch_fir_analysis(const void* f, int f_real, cplx<T>* c, const FirParams<cplx<T>>& fp,
@@ -202,16 +204,16 @@ cudaError_t p2_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T
                          int64_t B, cudaStream_t st);
 template <typename T>
 cudaError_t p2_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
-                            const void* tw, int64_t B, cudaStream_t st);
+                            const void* tw, int64_t B, unsigned int* expired, cudaStream_t st);
 template <typename T>
 cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
                        const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
 // Bounded device waits (the tensor-copy staging of fft_prod_adj): the wait limit in clock
-// cycles that launches pass to the kernels (a test hook lowers it), and the number of CTAs
-// whose wait expired since the last call (read and reset; synchronises the device).
+// cycles that launches pass to the kernels (a test hook lowers it).  A CTA whose wait expires
+// sets the caller's word `expired` to 1 (a plan's host-mapped word, or the word at the start
+// of a caller workspace), so each expiry is traced to the plan or workspace of its launch.
 constexpr long long kWaitCycles = 2000000000LL;       // about a second
 extern long long g_wait_limit_cycles;
-int p2_take_wait_timeouts();
 // columns per chunk of the power-of-two FIR synthesis for FFT length M (0: not applicable)
 template <typename T> int64_t p2_fir_synthesis_cols(int64_t M, int64_t N, int64_t a, int64_t Lg);
 // lengths of the power-of-two column kernels

@@ -374,9 +374,9 @@ __global__ void __launch_bounds__(kThreadsBig) fft_prod_adj_kernel(const cplx<T>
 
 template <typename T>
 cudaError_t launch_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
-                                const FftRef& fd, int64_t B, cudaStream_t st) {
+                                const FftRef& fd, int64_t B, unsigned int* expired, cudaStream_t st) {
     {
-        const cudaError_t e = p2_fft_prod_adj<T>(y, zg, J, zf, g, fd.tw, B, st);
+        const cudaError_t e = p2_fft_prod_adj<T>(y, zg, J, zf, g, fd.tw, B, expired, st);
         if (e != cudaErrorNotSupported) return e;
     }
     using C = cplx<T>;
@@ -678,7 +678,7 @@ cudaError_t launch_fft_rows_test(const cplx<T>* in, cplx<T>* out, const FftRef& 
     template cudaError_t launch_pre_ifft<T>(const cplx<T>*, cplx<T>*, const SepGeom&, int64_t, const FftRef&,         \
                                             const PostParams<cplx<T>>&, int64_t, cudaStream_t);                       \
     template cudaError_t launch_fft_prod_adj<T>(const cplx<T>*, const cplx<T>*, int64_t, cplx<T>*, const SepGeom&,    \
-                                                const FftRef&, int64_t, cudaStream_t);                                \
+                                                const FftRef&, int64_t, unsigned int*, cudaStream_t);                 \
     template cudaError_t launch_fft_grad_window<T>(const cplx<T>*, const cplx<T>*, int64_t, cplx<T>*,                 \
                                                    const SepGeom&, const FftRef&, int64_t, cudaStream_t);             \
     template cudaError_t launch_zak_inv<T>(const cplx<T>*, int64_t, void*, int, int64_t, int64_t, int64_t,            \

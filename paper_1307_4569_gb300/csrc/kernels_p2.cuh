@@ -193,18 +193,19 @@ __global__ void __launch_bounds__(AdjCfg<T, N>::THREADS, AdjCfg<T, N>::MINB) fft
 // buffer whose Y values have just been read, during the transform; the Y tile two iterations
 // ahead follows once the products are summed.  Waits are bounded
 // (wait_limit cycles; 0 lets every wait expire at once, for tests); a CTA whose wait expires
-// lets its copies land, counts itself in g_tma_wait_timeouts and returns (the host reports
-// DGT_ERR_TIMEOUT).
+// lets its copies land, sets *expired (the launching plan's or workspace's word) and returns
+// (the host reports DGT_ERR_TIMEOUT).
 // ------------------------------------------------------------------------------------
-namespace {
-__device__ unsigned int g_tma_wait_timeouts = 0;
+__device__ __forceinline__ void note_expired(unsigned int* expired) {
+    *reinterpret_cast<volatile unsigned int*>(expired) = 1u;
+    __threadfence_system();
 }
 
 template <int N, bool ZGT>
 __global__ void __launch_bounds__(AdjCfg<float, N>::THREADS, AdjCfg<float, N>::MINB)
     fft_prod_adj_tma_p2(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap zgmap,
                         const float2* __restrict__ zg, float2* __restrict__ zf, SepGeom g, int64_t J,
-                        const float2* __restrict__ tw, long long wait_limit) {
+                        const float2* __restrict__ tw, long long wait_limit, unsigned int* expired) {
     using C = float2;
     using CF = AdjCfg<float, N>;
     constexpr int W = CF::W;
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(AdjCfg<float, N>::THREADS, AdjCfg<float, N>::M
             for (int m = 0; m < 16; ++m) v[m] = tile[(t + G * m) * W + c];
             if (__syncthreads_or(late)) {         // also: every thread has read its Y values
                 if (threadIdx.x == 0) {
-                    atomicAdd(&g_tma_wait_timeouts, 1u);
+                    note_expired(expired);
                     drain(it, true, false);
                 }
                 return;
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(AdjCfg<float, N>::THREADS, AdjCfg<float, N>::M
             const bool late = wait_limit == 0 || !mbar_wait(barY + s, ph, wait_limit);
             if (__syncthreads_or(late)) {
                 if (threadIdx.x == 0) {
-                    atomicAdd(&g_tma_wait_timeouts, 1u);
+                    note_expired(expired);
                     drain(it, true, false);
                 }
                 return;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(AdjCfg<float, N>::THREADS, AdjCfg<float, N>::M
         if constexpr (ZGT) {
             if (__syncthreads_or(lateZ)) {
                 if (threadIdx.x == 0) {
-                    atomicAdd(&g_tma_wait_timeouts, 1u);
+                    note_expired(expired);
                     drain(it, false, true);
                 }
                 return;
@@ -675,6 +676,102 @@ __global__ void __launch_bounds__(AnaCfg<N>::THREADS, sizeof(T) == 4 && !MULTI ?
     }
 }
 
+// FIR analysis of real signals with a real window on lattices with lambda2 <= 2 (real-input
+// pairing).  With delta = w(n) in {0, 1/2} and l = ln + tap, tap = k - lnm (+ N when k < lnm),
+// lnm = ln mod N, the modulation exp(-2 pi i tap delta / N) of the FFT input splits into
+// e(k) = exp(-2 pi i k delta / N), the column constant exp(2 pi i lnm delta / N) and the sign
+// (-1)^[k < lnm] (delta = 1/2): column n's input is a real sequence r_n(k) (the sign folded in)
+// times e(k), and its coefficients are R_n(m + delta) times exp(2 pi i lnm delta / N)
+// exp(-2 pi i ln delta / N) = (-1)^floor(ln / N) (delta = 1/2) or 1, R_n(mu) =
+// sum_k r_n(k) exp(-2 pi i k mu / N).  Two columns n1, n1 + lambda2 of one w share the FFT of
+// (r1 + i r2) e(k), whose outputs are Z(m) = R1(m + delta) + i R2(m + delta); a real sequence
+// has R(-mu) = conj(R(mu)), so with P(m) = N - 1 - m (delta = 1/2) or -m mod N (delta = 0)
+// R1 = (Z(m) + conj(Z(P(m)))) / 2 and R2 = (Z(m) - conj(Z(P(m)))) / 2i, one exchange through
+// shared memory apart.  Pair p of a signal holds columns n1 = (p div lambda2) 2 lambda2 +
+// p mod lambda2 and n1 + lambda2; a CTA's RPB pairs cover 2 RPB consecutive columns, whose
+// common segment of (2 RPB - 1) a + Lg samples is staged in shared memory first.
+template <typename T, int N>
+__global__ void __launch_bounds__(AnaCfg<N>::THREADS, sizeof(T) == 4 ? AnaCfg<N>::MINB : 1)
+    fir_analysis_pair_p2(const T* __restrict__ f, cplx<T>* __restrict__ c, FirParams<cplx<T>> fp,
+                         int64_t pairs_total, const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using RC = AnaCfg<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / RC::G, t = threadIdx.x % RC::G;
+    C* sm = reinterpret_cast<C*>(smem_raw) + gi * Pow2<N>::SMEM;
+    T* seg = reinterpret_cast<T*>(smem_raw + sizeof(C) * (size_t)Pow2<N>::SMEM * RC::RPB);
+    const int lam2 = (int)fp.lam2;
+    const int64_t half = fp.N / 2;                              // pairs per signal
+    const int64_t P0 = (int64_t)blockIdx.x * RC::RPB;           // the CTA's first pair (same signal for all)
+    const int64_t b = P0 / half;
+    const int64_t p0 = P0 - b * half;
+    const int64_t nmin = (p0 / lam2) * 2 * lam2;                // first column of the CTA
+    const int64_t pp = p0 + gi;
+    const int64_t n1 = (pp / lam2) * 2 * lam2 + pp % lam2, n2 = n1 + lam2;
+    const bool ok = P0 + gi < pairs_total;
+    const int Lg = (int)fp.Lg;
+    const bool dh = (n1 * fp.lam1) % lam2 != 0;                 // delta = 1/2 (uniform per group)
+    // segment of the CTA: samples ln(nmin) + i, i < S
+    {
+        const int S = (2 * RC::RPB - 1) * (int)fp.a + Lg;
+        int64_t l0 = fp.a * nmin - fp.center;
+        if (l0 < 0) l0 += fp.L;
+        const T* fr = f + b * fp.L;
+        for (int i = threadIdx.x; i < S; i += RC::THREADS) {
+            int64_t l = l0 + i;
+            if (l >= fp.L) l -= fp.L;
+            seg[i] = fr[l];
+        }
+    }
+    __syncthreads();
+    auto col_time = [&](int64_t n) {
+        int64_t ln = fp.a * n - fp.center;
+        return ln < 0 ? ln + fp.L : ln;
+    };
+    const int64_t ln1 = col_time(n1), ln2 = col_time(n2);
+    const int lnm1 = (int)(ln1 & (N - 1)), lnm2 = (int)(ln2 & (N - 1));
+    const T* s1 = seg + (n1 - nmin) * fp.a;
+    const T* s2 = seg + (n2 - nmin) * fp.a;
+    const C* h = fp.mtaps;                                      // row wn = 0: the real taps
+    C v[16];
+    fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
+        const int tap1 = (k - lnm1) & (N - 1), tap2 = (k - lnm2) & (N - 1);
+        T x1 = (T)0, x2 = (T)0;
+        if (tap1 < Lg) {
+            x1 = s1[tap1] * __ldg(&h[tap1].x);
+            if (dh && k < lnm1) x1 = -x1;
+        }
+        if (tap2 < Lg) {
+            x2 = s2[tap2] * __ldg(&h[tap2].x);
+            if (dh && k < lnm2) x2 = -x2;
+        }
+        C z = mk(x1, x2);
+        if (dh) z = cmul(z, __ldg(fp.hb + k));
+        return z;
+    }, v);
+    // exchange: every output of the group's transform into its buffer (the transform's last
+    // reads of that buffer came before its final barrier)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) sm[spad(p2_out_pos<N>(t, i))] = v[i];
+    __syncthreads();
+    if (!ok) return;
+    const T g1 = dh && ((ln1 / N) & 1) ? (T)-0.5 : (T)0.5;     // column constants, with the 1/2
+    const T g2 = dh && ((ln2 / N) & 1) ? (T)-0.5 : (T)0.5;
+    const int64_t rs = fp.half ? N / 2 + 1 : N;
+    C* c1 = c + (b * fp.N + n1) * rs;
+    C* c2 = c + (b * fp.N + n2) * rs;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int m = p2_out_pos<N>(t, i);
+        if (fp.half && m > N / 2) continue;
+        const int pm = dh ? N - 1 - m : ((N - m) & (N - 1));
+        const C zp = sm[spad(pm)];
+        // R1 = (Z + conj(Zp)) / 2,  R2 = (Z - conj(Zp)) / 2i
+        c1[m] = mk(g1 * (v[i].x + zp.x), g1 * (v[i].y - zp.y));
+        c2[m] = mk(g2 * (v[i].y + zp.y), g2 * (zp.x - v[i].x));
+    }
+}
+
 // FIR synthesis: per chunk of `cols` consecutive columns, the inverse FFT of each column (times
 // the conjugate column constant exp(+2 pi i ln wn / (lam2 M))) is scattered straight from the
 // registers into a shared accumulator of the chunk's segment of a (cols - 1) + Lg samples:
@@ -865,13 +962,14 @@ inline TensorMapEncodeTiled tensor_map_encoder() {
 // geometry is outside what the tile copies take (odd M, coordinates past 2^31, no encoder).
 template <int N>
 cudaError_t p2_fft_prod_adj_tma(const float2* y, const float2* zg, int64_t J, float2* zf, const SepGeom& g,
-                                const void* tw, int64_t B, cudaStream_t st) {
+                                const void* tw, int64_t B, unsigned int* expired, cudaStream_t st) {
     using CF = AdjCfg<float, N>;
     constexpr int W = CF::W;
     constexpr int BOXR = N < 256 ? N : 256;
     static_assert(W * sizeof(float2) % 16 == 0, "tile rows of whole 16-byte units");
     const TensorMapEncodeTiled enc = tensor_map_encoder();
-    if (!enc || g.M % 2 || g.d != N || B * J * N >= ((int64_t)1 << 31) || (reinterpret_cast<uintptr_t>(y) & 15))
+    if (!enc || !expired || g.M % 2 || g.d != N || B * J * N >= ((int64_t)1 << 31) ||
+        (reinterpret_cast<uintptr_t>(y) & 15))
         return cudaErrorNotSupported;
     const cuuint32_t box[3] = {(cuuint32_t)W, 1, (cuuint32_t)BOXR};
     const cuuint32_t estr[3] = {1, 1, 1};
@@ -899,16 +997,16 @@ cudaError_t p2_fft_prod_adj_tma(const float2* y, const float2* zg, int64_t J, fl
     cudaError_t e = p2_smem(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((g.M + W - 1) / W), (unsigned)B);
-    k<<<grid, CF::THREADS, smem, st>>>(ymap, zgmap, zg, zf, g, J, (const float2*)tw, g_wait_limit_cycles);
+    k<<<grid, CF::THREADS, smem, st>>>(ymap, zgmap, zg, zf, g, J, (const float2*)tw, g_wait_limit_cycles, expired);
     return cudaGetLastError();
 }
 
 template <typename T, int N>
 cudaError_t p2_fft_prod_adj_n(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
-                              const void* tw, int64_t B, cudaStream_t st) {
+                              const void* tw, int64_t B, unsigned int* expired, cudaStream_t st) {
     using CF = AdjCfg<T, N>;
     if constexpr (sizeof(T) == 4 && CF::HALVE && CF::W >= 2) {
-        const cudaError_t e = p2_fft_prod_adj_tma<N>(y, zg, J, zf, g, tw, B, st);
+        const cudaError_t e = p2_fft_prod_adj_tma<N>(y, zg, J, zf, g, tw, B, expired, st);
         if (e != cudaErrorNotSupported) return e;
     }
     auto k = fft_prod_adj_p2<T, N>;
@@ -973,6 +1071,21 @@ cudaError_t p2_fir_analysis_n(const void* f, int f_real, cplx<T>* c, const FirPa
                               int64_t B, cudaStream_t st) {
     using RC = AnaCfg<N>;
     size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * RC::RPB;
+    {
+        // real-input pairing: real signal and window, lambda2 <= 2, whole CTAs of pairs
+        const int64_t S2 = (2 * RC::RPB - 1) * fp.a + fp.Lg;
+        const size_t seg2 = sizeof(T) * (size_t)S2;
+        if (f_real && fp.pairable && fp.lam2 <= 2 && RC::RPB % fp.lam2 == 0 && fp.Lg <= N &&
+            fp.N % (2 * RC::RPB) == 0 && S2 <= fp.L && smem + seg2 <= kSmemBudget && (fp.lam2 == 1 || fp.hb)) {
+            auto k = fir_analysis_pair_p2<T, N>;
+            cudaError_t e = p2_smem(k, smem + seg2);
+            if (e != cudaSuccess) return e;
+            const int64_t pairs = B * fp.N / 2;
+            k<<<(unsigned)(pairs / RC::RPB), RC::THREADS, smem + seg2, st>>>((const T*)f, c, fp, pairs,
+                                                                            (const cplx<T>*)tw);
+            return cudaGetLastError();
+        }
+    }
     // staged segment: every CTA's columns in one signal, the segment shorter than the signal
     const int64_t S = (RC::RPB - 1) * fp.a + fp.Lg;
     const size_t segb = (f_real ? sizeof(T) : sizeof(cplx<T>)) * (size_t)S;
@@ -1094,9 +1207,9 @@ cudaError_t p2_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T
 }
 template <typename T>
 cudaError_t p2_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
-                            const void* tw, int64_t B, cudaStream_t st) {
+                            const void* tw, int64_t B, unsigned int* expired, cudaStream_t st) {
     if (g.p != 1) return cudaErrorNotSupported;
-    P2_SWITCH(g.d, return (p2_fft_prod_adj_n<T, NN>(y, zg, J, zf, g, tw, B, st)))
+    P2_SWITCH(g.d, return (p2_fft_prod_adj_n<T, NN>(y, zg, J, zf, g, tw, B, expired, st)))
 }
 template <typename T>
 cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,

@@ -4,14 +4,7 @@
 namespace dgt {
 template cudaError_t p2_zak_fwd<float>(const void*, int, int64_t, cplx<float>*, int64_t, int64_t, int64_t, const void*, const ChirpParams<cplx<float>>&, int64_t, cudaStream_t);
 template cudaError_t p2_prod_ifft<float>(const cplx<float>*, const cplx<float>*, int64_t, cplx<float>*, const SepGeom&, const void*, int64_t, cudaStream_t);
-template cudaError_t p2_fft_prod_adj<float>(const cplx<float>*, const cplx<float>*, int64_t, cplx<float>*, const SepGeom&, const void*, int64_t, cudaStream_t);
+template cudaError_t p2_fft_prod_adj<float>(const cplx<float>*, const cplx<float>*, int64_t, cplx<float>*, const SepGeom&, const void*, int64_t, unsigned int*, cudaStream_t);
 template cudaError_t p2_zak_inv<float>(const cplx<float>*, int64_t, void*, int, int64_t, int64_t, int64_t, const void*, const ChirpParams<cplx<float>>&, float, int64_t, cudaStream_t);
-// CTAs of fft_prod_adj_tma_p2 (instantiated in this unit only) whose bounded wait expired
-int p2_take_wait_timeouts() {
-    unsigned int n = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&n, g_tma_wait_timeouts, sizeof(n)) != cudaSuccess) return 0;
-    if (n) cudaMemcpyToSymbol(g_tma_wait_timeouts, &zero, sizeof(zero));
-    return (int)n;
-}
 template cudaError_t p2_zak_prod_ifft<float>(const void*, int, int64_t, const cplx<float>*, int64_t, cplx<float>*, const SepGeom&, const void*, const ChirpParams<cplx<float>>&, int64_t, cudaStream_t);
 }  // namespace dgt

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -272,6 +273,51 @@ template <typename T> static int make_cis(CisBuf<T>& cb, int64_t den, cudaStream
 }
 
 // ---------------------------------------------------------------------------------------
+// expiry words of the bounded device waits: one host-mapped word per plan, handed out from
+// pinned pages that live until the process exits (so destroying a plan frees no pinned
+// memory); the synthesis kernels write 1 into the word of the plan they run for
+// ---------------------------------------------------------------------------------------
+static std::mutex g_expiry_mu;
+static std::vector<unsigned int*> g_expiry_free;
+static std::vector<unsigned int*> g_expiry_live;
+
+static int expiry_word_take(unsigned int** out) {
+    std::lock_guard<std::mutex> lock(g_expiry_mu);
+    if (g_expiry_free.empty()) {
+        constexpr size_t kWords = 1024;
+        void* page = nullptr;
+        CUDA_TRY(cudaHostAlloc(&page, kWords * sizeof(unsigned int), cudaHostAllocMapped | cudaHostAllocPortable));
+        unsigned int* w = (unsigned int*)page;
+        for (size_t i = 0; i < kWords; ++i) {
+            w[i] = 0;
+            g_expiry_free.push_back(w + i);
+        }
+    }
+    *out = g_expiry_free.back();
+    g_expiry_free.pop_back();
+    **out = 0;
+    g_expiry_live.push_back(*out);
+    return DGT_OK;
+}
+static void expiry_word_give(unsigned int* w) {
+    if (!w) return;
+    std::lock_guard<std::mutex> lock(g_expiry_mu);
+    g_expiry_live.erase(std::remove(g_expiry_live.begin(), g_expiry_live.end(), w), g_expiry_live.end());
+    g_expiry_free.push_back(w);
+}
+// read and clear a word (host side; the word is written by kernels through its mapping)
+static unsigned int expiry_word_take_value(unsigned int* w) {
+    if (!w) return 0;
+    volatile unsigned int* v = w;
+    const unsigned int x = *v;
+    if (x) *v = 0;
+    return x;
+}
+
+// the first bytes of a caller workspace hold its expiry word; the plan's work area follows
+constexpr size_t kWsHeader = 256;
+
+// ---------------------------------------------------------------------------------------
 // the plan
 // ---------------------------------------------------------------------------------------
 struct PlanCore {
@@ -293,20 +339,40 @@ struct PlanCore {
     std::vector<double> g_host;        // window as given (complex interleaved, float64)
     SepGeom coset_sep{};               // (lam2 a, M): used by the dual / tight Gram blocks
     int64_t ola_block = 0, ola_len = 0;  // blockwise plans: block length and local length
+    int device = -1;                   // the CUDA device current at creation (owns the plan's memory)
 };
 
 struct dgt_plan_s {
-    virtual ~dgt_plan_s() = default;
+    virtual ~dgt_plan_s() { expiry_word_give(expired); }
     PlanCore core;
+    unsigned int* expired = nullptr;   // host-mapped expiry word of the calls without a caller workspace
     virtual int exec(const void* f, int f_real, void* c, int64_t B, void* ws, cudaStream_t st) = 0;
-    virtual int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* ws, cudaStream_t st) = 0;
+    // `expired`: the word the synthesis kernels set when a bounded wait expires
+    virtual int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* ws, unsigned int* expired,
+                      cudaStream_t st) = 0;
     virtual int window_out(int which, void* out, cudaStream_t st) = 0;
+    virtual int iexec_window(const void* c, void* f, int f_real, int64_t B, const void* gamma, int gamma_real,
+                             cudaStream_t st) {
+        return fail(DGT_ERR_UNSUPPORTED, "synthesis with a caller's window is not available for this plan kind");
+    }
     virtual int set_window(const void* g, int is_real, cudaStream_t st) = 0;
     virtual int grad_window(const void* f, int f_real, const void* G, void* grad, int grad_real, int64_t B,
                             cudaStream_t st) = 0;
     virtual int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) = 0;
     virtual int fir_synthesis_noalloc(const void* c, void* f, int f_real, int64_t B, int which, cudaStream_t st) = 0;
-    virtual int status_check(cudaStream_t st) = 0;
+    // synchronise st; a pending CUDA error, or an expired wait of this plan's own calls
+    int status_check(cudaStream_t st) {
+        CUDA_TRY(cudaStreamSynchronize(st));
+        CUDA_TRY(cudaGetLastError());
+        return pending_expiry();
+    }
+    // an expiry recorded by earlier work of this plan (no synchronisation: reported at the
+    // next call once the kernel's write has landed); clears the word
+    int pending_expiry() {
+        if (expiry_word_take_value(expired))
+            return fail(DGT_ERR_TIMEOUT, "a synthesis kernel of this plan gave up waiting for its tile copies");
+        return DGT_OK;
+    }
     virtual size_t ws_bytes(int64_t B) const = 0;
     virtual size_t owned_bytes() const = 0;
     // real-signal analysis / synthesis on channels 0..M/2 (through a plan-owned full array)
@@ -338,7 +404,7 @@ static int iexec_real_via(dgt_plan_s* p, const void* ch, void* f, int64_t B, int
     DGT_TRY(p->real_full.alloc(sizeof(cplx<T>) * (size_t)B * k.N * k.M));
     KTRY("half_expand", st, launch_half_expand<T>((const cplx<T>*)ch, (cplx<T>*)p->real_full.p, k.N, k.M, k.lam1, k.lam2,
                                                   B, st));
-    return p->iexec(p->real_full.p, f, 1, B, which, nullptr, st);
+    return p->iexec(p->real_full.p, f, 1, B, which, nullptr, p->expired, st);
 }
 
 template <typename T> struct PlanImpl final : dgt_plan_s {
@@ -348,14 +414,15 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     DevBuf sigma;                      // coset shifts (int64, J)
     DevBuf g64;                        // window, float64 complex (L, or Lg taps for FIR)
     DevBuf gT;                         // window in T (L or Lg)
-    DevBuf zg[3];                      // window factors: 0 analysis/adjoint, 1 dual, 2 tight
-    bool zg_ok[3] = {false, false, false};
-    DevBuf gam[3];                     // gamma in T (full length L, or Lg taps for FIR)
+    DevBuf zg[4];                      // window factors: 0 analysis/adjoint, 1 dual, 2 tight, 3 caller's
+    bool zg_ok[4] = {false, false, false, false};
+    DevBuf gam[4];                     // gamma in T (full length L, or Lg taps for FIR)
     DevBuf work;                       // plan-owned workspace
     DevBuf tmpwin;                     // scratch for window set-up
     DevBuf status;                     // int flag for the Gram solve
-    DevBuf firmt[3];                   // FIR route: modulated taps [lam2][Lg] of the windows in gam / gT
+    DevBuf firmt[4];                   // FIR route: modulated taps [lam2][Lg] of the windows in gam / gT
     DevBuf lossparts;
+    DevBuf hbtab;                      // FIR route, lambda2 = 2: exp(-pi i k / M), k < M (real-input pairing)
 
     const FftRef* fft(int64_t n) {
         auto it = tw.find(n);
@@ -410,8 +477,8 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     size_t ws_bytes(int64_t B) const override { return layout(B).total; }
     size_t owned_bytes() const override {
         size_t s = sigma.bytes + g64.bytes + gT.bytes + work.bytes + tmpwin.bytes + status.bytes + lossparts.bytes +
-                   real_full.bytes;
-        for (int i = 0; i < 3; ++i) s += zg[i].bytes + gam[i].bytes + firmt[i].bytes;
+                   real_full.bytes + hbtab.bytes;
+        for (int i = 0; i < 4; ++i) s += zg[i].bytes + gam[i].bytes + firmt[i].bytes;
         for (auto& kv : tw) s += kv.second->buf.bytes;
         s += cisL.hi.bytes + cisL.lo.bytes + cis2L.hi.bytes + cis2L.lo.bytes + cis2N.hi.bytes + cis2N.lo.bytes +
              cisLM.hi.bytes + cisLM.lo.bytes;
@@ -491,6 +558,11 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         // FFT tables
         if (k.route == DGT_ROUTE_FIR) {
             DGT_TRY(add_fft(k.M, st));
+            if (k.lam2 == 2) {
+                std::vector<double> hb(2 * (size_t)k.M);
+                for (int64_t e = 0; e < k.M; ++e) cis_host(-e, 2 * k.M, hb[2 * e], hb[2 * e + 1]);
+                DGT_TRY(upload_cplx<T>(hbtab, hb, st));
+            }
         } else {
             DGT_TRY(add_fft(k.sep.d, st));
             DGT_TRY(add_fft(k.sep.M, st, true));
@@ -633,6 +705,8 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         fp.mtaps = (const C*)firmt[which].p;
         fp.mN = make_mod((uint64_t)k.N);
         fp.group = k.fir_group;
+        fp.pairable = which <= 2 && k.win_real;
+        fp.hb = (const C*)hbtab.p;
         return fp;
     }
 
@@ -718,12 +792,34 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         return DGT_OK;
     }
 
-    int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, cudaStream_t st) override {
-        return iexec_core(c, f, f_real, B, which, wsp, st, false);
+    int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, unsigned int* expired,
+              cudaStream_t st) override {
+        return iexec_core(c, f, f_real, B, which, wsp, expired, st, false);
     }
-    int iexec_core(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, cudaStream_t st, bool half) {
+    // synthesis with the caller's window (slot 3): its factorisation is built on `st` first
+    int iexec_window(const void* c, void* f, int f_real, int64_t B, const void* gamma, int gamma_real,
+                     cudaStream_t st) override {
         const PlanCore& k = core;
-        if (which < 0 || which > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which);
+        if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+        const bool fir = k.route == DGT_ROUTE_FIR;
+        const int64_t n = fir ? k.Lg : k.L;
+        zg_ok[3] = false;
+        DGT_TRY(gam[3].alloc(sizeof(C) * n));
+        CUDA_TRY(launch_convert<T, T>(gamma, gamma_real, (C*)gam[3].p, n, st));
+        if (fir) {
+            DGT_TRY(tmpwin.alloc(sizeof(double2) * n));
+            CUDA_TRY(launch_convert<T, double>(gamma, gamma_real, (double2*)tmpwin.p, n, st));
+            DGT_TRY(build_fir_mt(3, (const double2*)tmpwin.p, st));
+            zg_ok[3] = true;
+        } else {
+            DGT_TRY(build_factor(3, (const C*)gam[3].p, st));
+        }
+        return iexec_core(c, f, f_real, B, 3, nullptr, expired, st, false);
+    }
+    int iexec_core(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, unsigned int* expired,
+                   cudaStream_t st, bool half) {
+        const PlanCore& k = core;
+        if (which < 0 || which > 3) return fail(DGT_ERR_ARG, "bad synthesis window %d", which);
         if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
         if (!zg_ok[which]) {
             if (wsp) return fail(DGT_ERR_ARG, "the dual / tight window is not cached yet (call dgt_window_dual/_tight)");
@@ -750,7 +846,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         PostParams<C> ppi = post();
         ppi.half = half;
         KTRY("pre_ifft", st, launch_pre_ifft<T>((const C*)c, y, k.sep, k.J, *fft(k.sep.M), ppi, B, st));
-        KTRY("fft_prod_adj", st, launch_fft_prod_adj<T>(y, (const C*)zg[which].p, k.J, zf, k.sep, *fd, B, st));
+        KTRY("fft_prod_adj", st, launch_fft_prod_adj<T>(y, (const C*)zg[which].p, k.J, zf, k.sep, *fd, B, expired, st));
         if (k.route == DGT_ROUTE_COSET) {
             KTRY("zak_inv", st, launch_zak_inv<T>(zf, k.L, f, f_real, k.L, k.L, k.sep.d, *fd, nochirp(), (T)1, B, st));
         } else if (!k.freq_shear) {
@@ -827,13 +923,6 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         return DGT_OK;
     }
 
-    int status_check(cudaStream_t st) override {
-        CUDA_TRY(cudaStreamSynchronize(st));
-        CUDA_TRY(cudaGetLastError());
-        if (const int n = p2_take_wait_timeouts())
-            return fail(DGT_ERR_TIMEOUT, "%d CTAs gave up waiting for their tile copies", n);
-        return DGT_OK;
-    }
     // the power-of-two kernels read / write channels 0..M/2 directly: the FIR kernels, and
     // the channel FFT of the coset and time-shear routes (analysis) or its adjoint (synthesis)
     bool half_io(bool synthesis) const {
@@ -850,7 +939,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     int iexec_real(const void* ch, void* f, int64_t B, int which, cudaStream_t st) override {
         if (!half_io(true)) return iexec_real_via<T>(this, ch, f, B, which, st);
         DGT_TRY(real_ok(core));
-        return iexec_core(ch, f, 1, B, which, nullptr, st, true);
+        return iexec_core(ch, f, 1, B, which, nullptr, expired, st, true);
     }
 
     // FIR synthesis whose seam scratch is the library's fixed per-GPU array: no allocation.
@@ -869,9 +958,15 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         if (need > kNoAllocScratchBytes)
             return fail(DGT_ERR_UNSUPPORTED, "allocation-free synthesis needs %zu bytes of scratch; the fixed array holds %zu",
                         need, kNoAllocScratchBytes);
+        // the fixed array of the plan's device (its taps and tables live there too)
+        int cur = -1;
+        CUDA_TRY(cudaGetDevice(&cur));
+        if (cur != k.device)
+            return fail(DGT_ERR_ARG, "allocation-free synthesis on device %d for a plan of device %d: make the plan's "
+                        "device current", cur, k.device);
         void* scratch = nullptr;
         CUDA_TRY(noalloc_scratch(&scratch));
-        CUDA_TRY(launch_fir_synthesis<T>((const C*)c, f, f_real, (C*)scratch, fp, *fft(k.M), B, st));
+        KTRY("fir_synthesis_noalloc", st, launch_fir_synthesis<T>((const C*)c, f, f_real, (C*)scratch, fp, *fft(k.M), B, st));
         return DGT_OK;
     }
 
@@ -934,6 +1029,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
     k.L = L; k.a = a; k.M = M; k.lam1 = lam1; k.lam2 = lam2;
     k.b = L / M; k.N = L / a; k.s = k.b * lam1 / lam2;
     k.precision = precision;
+    CUDA_TRY(cudaGetDevice(&k.device));
     k.win_kind = g->kind;
     k.Lg = g->len;
     k.center = g->kind == DGT_WINDOW_FIR ? g->center : 0;
@@ -1061,6 +1157,7 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
         s = q->init(st);
         p = q;
     }
+    if (s == DGT_OK) s = expiry_word_take(&p->expired);
     if (s != DGT_OK) {
         delete p;
         return s;
@@ -1106,7 +1203,8 @@ template <typename T> struct OlaPlan final : dgt_plan_s {
         KTRY("ola_add", st, launch_ola_add<T>((const C*)(ws + ly.cx), (C*)c, og, B, st));
         return DGT_OK;
     }
-    int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, cudaStream_t st) override {
+    int iexec(const void* c, void* f, int f_real, int64_t B, int which, void* wsp, unsigned int* expired,
+              cudaStream_t st) override {
         if (which < 0 || which > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which);
         if (B <= 0) return B == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
         if (which) {
@@ -1118,7 +1216,7 @@ template <typename T> struct OlaPlan final : dgt_plan_s {
         char* ws = workspace(B, wsp);
         if (!ws) return DGT_ERR_OOM;
         KTRY("ola_gather", st, launch_ola_gather<T>((const C*)c, (C*)(ws + ly.cx), og, B, st));
-        DGT_TRY(inner->iexec(ws + ly.cx, ws + ly.x, f_real, B * og.Nb, which, ws + ly.in, st));
+        DGT_TRY(inner->iexec(ws + ly.cx, ws + ly.x, f_real, B * og.Nb, which, ws + ly.in, expired, st));
         KTRY("ola_take", st, launch_ola_take<T>(ws + ly.x, f_real, f, og, B, st));
         return DGT_OK;
     }
@@ -1153,7 +1251,6 @@ template <typename T> struct OlaPlan final : dgt_plan_s {
     int fir_synthesis_noalloc(const void*, void*, int, int64_t, int, cudaStream_t) override {
         return fail(DGT_ERR_ARG, "allocation-free synthesis needs an FIR-route plan");
     }
-    int status_check(cudaStream_t st) override { return inner->status_check(st); }
     int exec_real(const void* f, void* ch, int64_t B, cudaStream_t st) override {
         return exec_real_via<T>(this, f, ch, B, st);
     }
@@ -1217,6 +1314,11 @@ static int create_ola_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int
         p->core = k;
         *out = p;
     }
+    if (const int e = expiry_word_take(&(*out)->expired)) {
+        delete *out;
+        *out = nullptr;
+        return e;
+    }
     return DGT_OK;
 }
 
@@ -1253,9 +1355,9 @@ struct dgt2_plan_s {
         C* t2 = (C*)((char*)work.p + al(sizeof(C) * n12));
         C* t3 = (C*)((char*)work.p + 2 * al(sizeof(C) * n12));
         KTRY("transpose", st, launch_transpose<T>((const C*)c, t3, K1, K2, B, st));   // [B][N2 M2][N1 M1]
-        DGT_TRY(p1->iexec(t3, t2, 0, B * K2, which, nullptr, st));                   // [B][N2 M2][L1]
+        DGT_TRY(p1->iexec(t3, t2, 0, B * K2, which, nullptr, p1->expired, st));     // [B][N2 M2][L1]
         KTRY("transpose", st, launch_transpose<T>(t2, t1, K2, L1, B, st));           // [B][L1][N2 M2]
-        return p2->iexec(t1, f, f_real, B * L1, which, nullptr, st);                 // [B][L1][L2]
+        return p2->iexec(t1, f, f_real, B * L1, which, nullptr, p2->expired, st);   // [B][L1][L2]
     }
 };
 
@@ -1358,44 +1460,70 @@ int dgt_plan_set_window(dgt_plan_t plan, const void* g_dev, int is_real, void* s
 
 int dgt_exec(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* stream) {
     if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    DGT_TRY(plan->pending_expiry());
     return plan->exec(f, f_is_real, c, batch, nullptr, (cudaStream_t)stream);
 }
 
 int idgt_exec(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window, void* stream) {
     if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
-    return plan->iexec(c, f, f_real_out, batch, which_window, nullptr, (cudaStream_t)stream);
+    DGT_TRY(plan->pending_expiry());
+    return plan->iexec(c, f, f_real_out, batch, which_window, nullptr, plan->expired, (cudaStream_t)stream);
+}
+
+int idgt_exec_window(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, const void* gamma,
+                     int gamma_is_real, void* stream) {
+    if (!plan || !gamma || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    DGT_TRY(plan->pending_expiry());
+    return plan->iexec_window(c, f, f_real_out, batch, gamma, gamma_is_real, (cudaStream_t)stream);
 }
 
 int dgt_exec_real(dgt_plan_t plan, const void* f, void* c, int64_t batch, void* stream) {
     if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    DGT_TRY(plan->pending_expiry());
     return plan->exec_real(f, c, batch, (cudaStream_t)stream);
 }
 
 int idgt_exec_real(dgt_plan_t plan, const void* c, void* f, int64_t batch, int which_window, void* stream) {
     if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
     if (which_window < 0 || which_window > 2) return fail(DGT_ERR_ARG, "bad synthesis window %d", which_window);
+    DGT_TRY(plan->pending_expiry());
     return plan->iexec_real(c, f, batch, which_window, (cudaStream_t)stream);
 }
 
 int dgt_workspace_bytes(dgt_plan_t plan, int64_t batch, size_t* bytes) {
     if (!plan || !bytes || batch < 0) return fail(DGT_ERR_ARG, "bad argument");
-    *bytes = plan->ws_bytes(batch);
+    *bytes = kWsHeader + plan->ws_bytes(batch);
     return DGT_OK;
 }
 
 int dgt_exec_ws(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* workspace, void* stream) {
-    if (!plan || (!f && batch) || (!c && batch) || (!workspace && plan->ws_bytes(batch)))
-        return fail(DGT_ERR_ARG, "null pointer");
+    if (!plan || (!f && batch) || (!c && batch) || !workspace) return fail(DGT_ERR_ARG, "null pointer");
     if (((uintptr_t)workspace) & 255) return fail(DGT_ERR_ARG, "workspace must be 256-byte aligned");
-    return plan->exec(f, f_is_real, c, batch, workspace ? workspace : (void*)1, (cudaStream_t)stream);
+    return plan->exec(f, f_is_real, c, batch, (char*)workspace + kWsHeader, (cudaStream_t)stream);
 }
 
 int idgt_exec_ws(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
                  void* workspace, void* stream) {
-    if (!plan || (!f && batch) || (!c && batch) || (!workspace && plan->ws_bytes(batch)))
-        return fail(DGT_ERR_ARG, "null pointer");
+    if (!plan || (!f && batch) || (!c && batch) || !workspace) return fail(DGT_ERR_ARG, "null pointer");
     if (((uintptr_t)workspace) & 255) return fail(DGT_ERR_ARG, "workspace must be 256-byte aligned");
-    return plan->iexec(c, f, f_real_out, batch, which_window, workspace ? workspace : (void*)1, (cudaStream_t)stream);
+    if (batch <= 0) return batch == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+    // this call's expiry word: the first word of the workspace, cleared in stream order
+    CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(unsigned int), (cudaStream_t)stream));
+    return plan->iexec(c, f, f_real_out, batch, which_window, (char*)workspace + kWsHeader, (unsigned int*)workspace,
+                       (cudaStream_t)stream);
+}
+
+int dgt_workspace_status(dgt_plan_t plan, const void* workspace, void* stream) {
+    if (!plan || !workspace) return fail(DGT_ERR_ARG, "null pointer");
+    unsigned int w = 0;
+    CUDA_TRY(cudaMemcpyAsync(&w, workspace, sizeof(w), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaGetLastError());
+    if (w) {
+        CUDA_TRY(cudaMemsetAsync(const_cast<void*>(workspace), 0, sizeof(w), (cudaStream_t)stream));
+        return fail(DGT_ERR_TIMEOUT, "a synthesis kernel of this workspace's call gave up waiting for its tile copies");
+    }
+    return DGT_OK;
 }
 
 int dgt_window_dual(dgt_plan_t plan, void* gamma_out, void* stream) {
@@ -1411,17 +1539,20 @@ int dgt_window_tight(dgt_plan_t plan, void* gt_out, void* stream) {
 int dgt_grad_window(dgt_plan_t plan, const void* f, int f_is_real, const void* G, void* grad_g, int grad_real,
                     int64_t batch, void* stream) {
     if (!plan || !f || !G || !grad_g || batch <= 0) return fail(DGT_ERR_ARG, "bad argument");
+    DGT_TRY(plan->pending_expiry());
     return plan->grad_window(f, f_is_real, G, grad_g, grad_real, batch, (cudaStream_t)stream);
 }
 
 int dgt_fir_synthesis_noalloc(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
                               void* stream) {
     if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    DGT_TRY(plan->pending_expiry());
     return plan->fir_synthesis_noalloc(c, f, f_real_out, batch, which_window, (cudaStream_t)stream);
 }
 
 int dgt_logmag_loss(dgt_plan_t plan, const void* c, void* G, double* loss_dev, double eps, int64_t batch, void* stream) {
     if (!plan || !c || !loss_dev || batch <= 0) return fail(DGT_ERR_ARG, "bad argument");
+    DGT_TRY(plan->pending_expiry());
     return plan->logmag(c, G, loss_dev, eps, batch, (cudaStream_t)stream);
 }
 
@@ -1439,8 +1570,12 @@ int dgt_plan_status(dgt_plan_t plan, void* stream) {
 int dgt_sync(void* stream) {
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     CUDA_TRY(cudaGetLastError());
-    if (const int n = p2_take_wait_timeouts())
-        return fail(DGT_ERR_TIMEOUT, "%d CTAs gave up waiting for their tile copies", n);
+    int n = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_expiry_mu);
+        for (unsigned int* w : g_expiry_live) n += expiry_word_take_value(w) ? 1 : 0;
+    }
+    if (n) return fail(DGT_ERR_TIMEOUT, "synthesis kernels of %d plans gave up waiting for their tile copies", n);
     return DGT_OK;
 }
 

@@ -387,15 +387,19 @@ class GpuExecutor:
                     ring[rid % self.RING].copy_(y[i], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        return (ev, x, y, ws, outs, p, si)
+        return (ev, x, y, ws, outs, p, si, kind)
 
     def done(self, h) -> bool:
         return h[0].query()
 
     def finish(self, h) -> None:
-        ev, x, y, ws, outs, p, si = h
+        ev, x, y, ws, outs, p, si, kind = h
         try:
             ev.synchronize()             # raises if the device reported an error for this stream
+            if kind == "idgt":
+                # a synthesis kernel that gave up waiting for its tile copies left part of this
+                # batch's output unwritten: the batch's workspace word says so (DGTError)
+                p.workspace_status(ws, stream=self.streams[si])
         finally:
             self.free.append(si)
         for rid, t in outs:

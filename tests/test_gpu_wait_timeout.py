@@ -25,9 +25,15 @@ def _built():
     build.build()
 
 
+def _seeded_coefs(L, a, M, B):
+    N = L // a
+    r = np.random.default_rng(515)
+    return (r.standard_normal((B, N, M)) + 1j * r.standard_normal((B, N, M))).astype(np.complex64)
+
+
 @pytest.mark.parametrize("route", ["coset", "shear"])
 def test_expired_waits_report_timeout_and_leave_the_context_usable(route):
-    from paper_1307_4569_gb300 import Plan
+    from paper_1307_4569_gb300 import DGTError, Plan
     from paper_1307_4569_gb300 import _capi as K
 
     # d = L / M = 1024: the adjoint's column transforms take the tile-staged kernel
@@ -35,15 +41,14 @@ def test_expired_waits_report_timeout_and_leave_the_context_usable(route):
     g = gaussian_window(L)
     p = Plan(L, a, M, l1, l2, g, route=route, precision="f32")
     assert p.info["d"] == 1024
-    f = torch.from_numpy(np.stack([complex_normal(L, 5, i) for i in range(2)]).astype(np.complex64)).cuda()
-    c = p.dgt(f)
+    uh = _seeded_coefs(L, a, M, 2)
+    c = torch.from_numpy(uh).cuda()
     ref = p.idgt(c, window="adjoint")
     torch.cuda.synchronize()
     p.status()
     # the adjoint against the oracle (the staged kernel is the one that ran)
     g32 = g.astype(np.float32).astype(np.float64)
-    u = c[0].cpu().numpy().astype(np.complex128)
-    want = OD.idgt_coset(u.T, g32, a, M, l1, l2)
+    want = OD.idgt_coset(uh[0].astype(np.complex128).T, g32, a, M, l1, l2)
     got = ref[0].cpu().numpy().astype(np.complex128)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 2e-6
     stream = torch.cuda.current_stream().cuda_stream
@@ -59,4 +64,38 @@ def test_expired_waits_report_timeout_and_leave_the_context_usable(route):
     torch.cuda.synchronize()
     p.status()
     assert torch.equal(again, ref)
+
+    # without a status call, the plan's next call reports the expiry (and enqueues nothing)
+    old = K.lib().dgt_wait_limit(0)
+    try:
+        p.idgt(c, window="adjoint")
+        torch.cuda.synchronize()
+    finally:
+        K.lib().dgt_wait_limit(old)
+    with pytest.raises(DGTError, match="DGT_ERR_TIMEOUT"):
+        p.idgt(c, window="adjoint")
+    assert torch.equal(p.idgt(c, window="adjoint"), ref)
+
+    # caller workspaces: the expiry lands in the word of the workspace its call used, not in
+    # the plan's word or another workspace's
+    nb = p.workspace_bytes(2)
+    ws1 = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    ws2 = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    out1, out2 = torch.empty_like(ref), torch.empty_like(ref)
+    p.idgt_ws(c, out2, "adjoint", False, ws2)
+    old = K.lib().dgt_wait_limit(0)
+    try:
+        p.idgt_ws(c, out1, "adjoint", False, ws1)
+        torch.cuda.synchronize()
+    finally:
+        K.lib().dgt_wait_limit(old)
+    with pytest.raises(DGTError, match="DGT_ERR_TIMEOUT"):
+        p.workspace_status(ws1)
+    p.workspace_status(ws1)                       # reported once
+    p.workspace_status(ws2)
+    p.status()
+    assert torch.equal(out2, ref)
+    p.idgt_ws(c, out1, "adjoint", False, ws1)
+    p.workspace_status(ws1)
+    assert torch.equal(out1, ref)
     p.close()
