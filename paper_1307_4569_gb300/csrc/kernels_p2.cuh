@@ -711,16 +711,25 @@ __global__ void __launch_bounds__(AnaCfg<N>::THREADS, sizeof(T) == 4 ? AnaCfg<N>
     const bool ok = P0 + gi < pairs_total;
     const int Lg = (int)fp.Lg;
     const bool dh = (n1 * fp.lam1) % lam2 != 0;                 // delta = 1/2 (uniform per group)
-    // segment of the CTA: samples ln(nmin) + i, i < S
+    // segment of the CTA: samples ln(nmin) + i, i < S; eight loads in flight per thread
     {
         const int S = (2 * RC::RPB - 1) * (int)fp.a + Lg;
         int64_t l0 = fp.a * nmin - fp.center;
         if (l0 < 0) l0 += fp.L;
         const T* fr = f + b * fp.L;
-        for (int i = threadIdx.x; i < S; i += RC::THREADS) {
-            int64_t l = l0 + i;
-            if (l >= fp.L) l -= fp.L;
-            seg[i] = fr[l];
+        constexpr int U = 8;
+        for (int i0 = threadIdx.x; i0 < S; i0 += U * RC::THREADS) {
+            T x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * RC::THREADS;
+                int64_t l = l0 + i;
+                if (l >= fp.L) l -= fp.L;
+                x[u] = i < S ? __ldg(fr + l) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (i0 + u * RC::THREADS < S) seg[i0 + u * RC::THREADS] = x[u];
         }
     }
     __syncthreads();
@@ -882,6 +891,141 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_p2(cons
         if (tt < ov) seamL[tt] = val;
         else if (tt >= S - ov) seamR[tt - (S - ov)] = val;
         else reinterpret_cast<A*>(f)[b * fp.L + l] = val;
+    }
+}
+
+// FIR synthesis with real output, real window, lambda2 <= 2 (real-output pairing).  With
+// delta = w(n) and tap = k - lnm (+ N when k < lnm), column n adds to f(ln + tap)
+//   h(tap) sigma_n (-1)^[k < lnm] q_n(k),   q_n(k) = Re sum_m c(m) exp(2 pi i k (m + delta) / N),
+// sigma_n = (-1)^floor(ln / N) when delta = 1/2, else 1 (the column constant and the tap
+// modulation combined, as in the paired analysis).  q_n is the transform of the Hermitian
+// part H(m) = (c(m) + conj(c(P(m)))) / 2, P(m) = N - 1 - m (delta = 1/2) or -m mod N, which is
+// real; so two columns of one w share the inverse FFT of H1 + i H2, times
+// exp(2 pi i k delta / N): its real part is q1, its imaginary part q2.  (Half rows of a real
+// signal's coefficients are already Hermitian: H is the expanded row.)  The pairs are columns
+// of rounds q and q + lambda2 (D = ceil(Lg / a), D a multiple of 2 lambda2, so both columns
+// of a pair have the same w); the first columns of all groups are scattered, a barrier, then
+// the second ones, a barrier (columns of one round never share a sample).
+template <typename T, int N, int DIV>
+__global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_pair_p2(const cplx<T>* __restrict__ c,
+                                                                            T* __restrict__ f,
+                                                                            T* __restrict__ seams,
+                                                                            FirParams<cplx<T>> fp,
+                                                                            const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using RC = SynCfg<N, DIV>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw) + (threadIdx.x / RC::G) * Pow2<N>::SMEM;
+    T* acc = reinterpret_cast<T*>(smem_raw + sizeof(C) * (size_t)Pow2<N>::SMEM * RC::RPB);
+    const int gi = threadIdx.x / RC::G, t = threadIdx.x % RC::G;
+    const int64_t b = blockIdx.y;
+    const int64_t chunk = blockIdx.x;
+    const int64_t nchunks = gridDim.x;
+    const int64_t n0 = chunk * fp.cols;
+    const int nc = (int)fp.cols;
+    const int a = (int)fp.a, Lg = (int)fp.Lg, lam2 = (int)fp.lam2;
+    const int S = a * (nc - 1) + Lg;
+    const int D = (Lg + a - 1) / a;
+    const int PR = nc / D;                           // columns per round
+    T* h = acc + S;                                  // the real taps
+    for (int i = threadIdx.x; i < S; i += RC::THREADS) acc[i] = (T)0;
+    for (int i = threadIdx.x; i < Lg; i += RC::THREADS) h[i] = fp.mtaps[i].x;
+    __syncthreads();
+    for (int dq = 0; dq < D / 2; ++dq) {
+        const int q1 = (dq / lam2) * 2 * lam2 + dq % lam2;
+        for (int s0 = 0; s0 < PR; s0 += RC::RPB) {
+            const int sidx = s0 + gi;
+            const bool ok = sidx < PR;
+            const int r1 = q1 + D * (ok ? sidx : 0), r2 = r1 + lam2;
+            const int64_t n1 = n0 + r1, n2 = n0 + r2;
+            const bool dh = (n1 * fp.lam1) % lam2 != 0;
+            C v[16];
+            if (fp.half) {
+                const C* c1 = c + (b * fp.N + n1) * (N / 2 + 1);
+                const C* c2 = c + (b * fp.N + n2) * (N / 2 + 1);
+                const int s2 = dh ? 1 : 0;           // channel m > N/2 is conj of channel (-m - 2 w) mod N
+                fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                    if (!ok) return mk((T)0, (T)0);
+                    const C h1 = m <= N / 2 ? c1[m] : cconj(c1[(-m - s2) & (N - 1)]);
+                    const C h2 = m <= N / 2 ? c2[m] : cconj(c2[(-m - s2) & (N - 1)]);
+                    return mk(h1.x - h2.y, h1.y + h2.x);
+                }, v);
+            } else {
+                const C* c1 = c + (b * fp.N + n1) * N;
+                const C* c2 = c + (b * fp.N + n2) * N;
+                fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                    if (!ok) return mk((T)0, (T)0);
+                    const int pm = dh ? N - 1 - m : ((N - m) & (N - 1));
+                    const C a1 = c1[m], p1 = c1[pm], a2 = c2[m], p2 = c2[pm];
+                    // H1 + i H2, H = (c(m) + conj(c(P(m)))) / 2
+                    return mk((T)0.5 * ((a1.x + p1.x) - (a2.y - p2.y)), (T)0.5 * ((a1.y - p1.y) + (a2.x + p2.x)));
+                }, v);
+            }
+            int64_t ln1 = fp.a * n1 - fp.center, ln2 = fp.a * n2 - fp.center;
+            if (ln1 < 0) ln1 += fp.L;
+            if (ln2 < 0) ln2 += fp.L;
+            const int lnm1 = (int)(ln1 & (N - 1)), lnm2 = (int)(ln2 & (N - 1));
+            const T sg1 = dh && ((ln1 / N) & 1) ? (T)-1 : (T)1;
+            const T sg2 = dh && ((ln2 / N) & 1) ? (T)-1 : (T)1;
+            if (dh) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const C e = __ldg(fp.hb + p2_out_pos<N>(t, i));      // exp(-pi i k / N)
+                    v[i] = mk(v[i].x * e.x + v[i].y * e.y, v[i].y * e.x - v[i].x * e.y);
+                }
+            }
+            {
+                // the rows of this group's next pair into L2 while the current pair is scattered
+                int dq2 = dq, s2i = s0 + RC::RPB;
+                if (s2i >= PR) { s2i = 0; ++dq2; }
+                const int sidx2 = s2i + gi;
+                if (dq2 < D / 2 && sidx2 < PR) {
+                    const int q2 = (dq2 / lam2) * 2 * lam2 + dq2 % lam2;
+                    const int64_t m1 = n0 + q2 + D * sidx2;
+                    const int64_t rs = fp.half ? N / 2 + 1 : N;
+                    const char* r1p = reinterpret_cast<const char*>(c + (b * fp.N + m1) * rs);
+                    const char* r2p = reinterpret_cast<const char*>(c + (b * fp.N + m1 + lam2) * rs);
+                    const int64_t lines = (rs * (int64_t)sizeof(C) + 127) / 128;
+                    for (int64_t li = t; li < lines; li += RC::G) {
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(r1p + li * 128));
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(r2p + li * 128));
+                    }
+                }
+            }
+            if (ok) {
+                T* ar = acc + r1 * a;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int k = p2_out_pos<N>(t, i);
+                    const int tap = (k - lnm1) & (N - 1);
+                    if (tap < Lg) ar[tap] += ((dh && k < lnm1) ? -sg1 : sg1) * h[tap] * v[i].x;
+                }
+            }
+            __syncthreads();                        // columns of the rounds q and q + lambda2 overlap
+            if (ok) {
+                T* ar = acc + r2 * a;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int k = p2_out_pos<N>(t, i);
+                    const int tap = (k - lnm2) & (N - 1);
+                    if (tap < Lg) ar[tap] += ((dh && k < lnm2) ? -sg2 : sg2) * h[tap] * v[i].y;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int ov = Lg > a ? Lg - a : 0;
+    int64_t lstart = fp.a * n0 - fp.center;
+    if (lstart < 0) lstart += fp.L;
+    T* seamL = seams + (b * nchunks + chunk) * 2 * ov;
+    T* seamR = seamL + ov;
+    for (int tt = threadIdx.x; tt < S; tt += RC::THREADS) {
+        int64_t l = lstart + tt;
+        if (l >= fp.L) l -= fp.L;
+        const T val = acc[tt];
+        if (tt < ov) seamL[tt] = val;
+        else if (tt >= S - ov) seamR[tt - (S - ov)] = val;
+        else f[b * fp.L + l] = val;
     }
 }
 
@@ -1148,9 +1292,38 @@ cudaError_t p2_fir_synthesis_launch(const cplx<T>* c, void* f, int f_real, cplx<
     return cudaGetLastError();
 }
 
+template <typename T, int N, int DIV>
+cudaError_t p2_fir_synthesis_pair_launch(const cplx<T>* c, void* f, cplx<T>* seams, const FirParams<cplx<T>>& fp,
+                                         const void* tw, int64_t B, cudaStream_t st) {
+    const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * SynCfg<N, DIV>::RPB +
+                        sizeof(T) * (size_t)(fp.a * (fp.cols - 1) + 2 * fp.Lg);
+    if (smem > kSmemBudget) return cudaErrorNotSupported;
+    auto k = fir_synthesis_pair_p2<T, N, DIV>;
+    cudaError_t e = p2_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(fp.N / fp.cols), (unsigned)B);
+    k<<<grid, SynCfg<N, DIV>::THREADS, smem, st>>>(c, (T*)f, (T*)seams, fp, (const cplx<T>*)tw);
+    return cudaGetLastError();
+}
+
 template <typename T, int N>
 cudaError_t p2_fir_synthesis_n(const cplx<T>* c, void* f, int f_real, cplx<T>* seams, const FirParams<cplx<T>>& fp,
                                const void* tw, int64_t B, cudaStream_t st) {
+    {
+        // real output, real window, lambda2 <= 2, rounds that pair up (D a multiple of 2 lambda2)
+        const int64_t D = (fp.Lg + fp.a - 1) / fp.a;
+        if (f_real && fp.pairable && fp.lam2 <= 2 && fp.Lg <= N && D % (2 * fp.lam2) == 0 && fp.cols % D == 0 &&
+            fp.N % fp.cols == 0 && (fp.lam2 == 1 || fp.hb)) {
+            cudaError_t e = cudaErrorNotSupported;
+            if (p2_fir_synthesis_small<T, N>(fp.cols, fp.N, fp.a, fp.Lg))
+                e = p2_fir_synthesis_pair_launch<T, N, 4>(c, f, seams, fp, tw, B, st);
+            else if (p2_fir_synthesis_fits<T, N, 1>(fp.cols, fp.N, fp.a, fp.Lg))
+                e = p2_fir_synthesis_pair_launch<T, N, 1>(c, f, seams, fp, tw, B, st);
+            else if (p2_fir_synthesis_fits<T, N, 4>(fp.cols, fp.N, fp.a, fp.Lg))
+                e = p2_fir_synthesis_pair_launch<T, N, 4>(c, f, seams, fp, tw, B, st);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    }
     if (p2_fir_synthesis_small<T, N>(fp.cols, fp.N, fp.a, fp.Lg))
         return p2_fir_synthesis_launch<T, N, 4>(c, f, f_real, seams, fp, tw, B, st);
     if (p2_fir_synthesis_fits<T, N, 1>(fp.cols, fp.N, fp.a, fp.Lg))

@@ -4,7 +4,10 @@ modulation split as in eq. rect-flops-FIR), against the oracle's fold form on ev
 coefficient: lambda2 = 1 and 2, columns whose taps wrap around the end of the signal (the
 first and last CTAs), an odd number of columns per w class (which takes the unpaired kernel),
 real-signal half rows, and a complex window and a complex signal on the same lattice (no
-pairing).  float32 2e-6, float64 1e-12 relative l2 per signal."""
+pairing).  The real-output synthesis pairs the same way (two columns of one w share an
+inverse FFT of their Hermitian parts): real output against the real part of the oracle's
+synthesis, with the window and with its dual, and the real-signal half rows through
+reconstruction.  float32 2e-6, float64 1e-12 relative l2 per signal."""
 import numpy as np
 import pytest
 
@@ -96,3 +99,37 @@ def test_fir_real_pairing(prec, lat):
     for b in range(B):
         assert _rel(cz[b], OD.dgt_fold(f[b], gz, a, M, l1, l2).T) <= TOL[prec]
     pz.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("lat", LATTICES, ids=lambda v: "L%d-a%d-M%d-l%d_%d-g%d" % v)
+def test_fir_real_output_synthesis_pairing(prec, lat):
+    from oracle import duals as OU
+    from paper_1307_4569_gb300 import Plan
+
+    L, a, M, l1, l2, Lg = lat
+    N = L // a
+    taps, center = hann_taps(Lg)
+    if Lg == 384:
+        center = 100
+    taps = _round(taps / np.linalg.norm(taps), prec)
+    g = _full(taps, center, L)
+    B = 3
+    r = np.random.default_rng((91, L))
+    c = _round(r.standard_normal((B, N, M)) + 1j * r.standard_normal((B, N, M)), prec)
+    p = Plan(L, a, M, l1, l2, taps, route="fir", precision=prec, fir_center=center)
+    cd = _dev(c, prec)
+    out = p.idgt(cd, window="adjoint", real=True).cpu().numpy()
+    for b in range(B):
+        assert _rel(out[b], OD.idgt_fold(c[b].T, g, a, M, l1, l2).real) <= TOL[prec], (lat, b)
+    if N * M >= 2 * L:                                   # redundancy >= 2: a frame with the diagonal dual
+        gd = OU.fir_dual_diag(g, a, M)
+        out = p.idgt(cd, window="dual", real=True).cpu().numpy()
+        for b in range(B):
+            assert _rel(out[b], OD.idgt_fold(c[b].T, gd, a, M, l1, l2).real) <= TOL[prec], (lat, b)
+        # half rows of a real signal's coefficients: perfect reconstruction
+        f = _round(np.stack([real_normal(L, 92, i) for i in range(B)]), prec)
+        back = p.idgtreal(p.dgtreal(_dev(f, prec)), window="dual").cpu().numpy()
+        for b in range(B):
+            assert _rel(back[b], f[b]) <= (1e-5 if prec == "f32" else 1e-12)
+    p.close()
