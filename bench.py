@@ -100,6 +100,57 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------------------------------
+# host memory placement of the end-to-end buffers
+# -------------------------------------------------------------------------------------
+def _cpulist(text):
+    out = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        if "-" in part:
+            lo, hi = part.split("-")
+            out.update(range(int(lo), int(hi) + 1))
+        else:
+            out.add(int(part))
+    return out
+
+
+def gpu_host_locality(index):
+    """(NUMA node, CPUs) that sysfs lists as local to the GPU's PCI function, or (None, None)."""
+    try:
+        bus = subprocess.check_output(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id",
+                                       "--format=csv,noheader"], text=True, timeout=20).strip()
+        dom, rest = bus.split(":", 1)
+        path = "/sys/bus/pci/devices/%04x:%s" % (int(dom, 16), rest.lower())
+        node = int(open(os.path.join(path, "numa_node")).read())
+        cpus = _cpulist(open(os.path.join(path, "local_cpulist")).read())
+        cpus &= os.sched_getaffinity(0)
+        return (node if node >= 0 else None), (cpus or None)
+    except Exception:
+        return None, None
+
+
+def page_nodes(tensors):
+    """NUMA nodes of the first page of each host tensor (move_pages with no target: a query)."""
+    import ctypes
+    import platform
+
+    nr = {"aarch64": 239, "x86_64": 279}.get(platform.machine())
+    if nr is None:
+        return None
+    try:
+        libc = ctypes.CDLL(None, use_errno=True)
+        n = len(tensors)
+        pages = (ctypes.c_void_p * n)(*[t.data_ptr() for t in tensors])
+        status = (ctypes.c_int * n)()
+        if libc.syscall(nr, 0, n, pages, None, status, 0) != 0:
+            return None
+        return sorted({int(v) for v in status})
+    except Exception:
+        return None
+
+
+# -------------------------------------------------------------------------------------
 # replicas: one process per GPU, each on its own signals; no data-path collective
 # -------------------------------------------------------------------------------------
 def replica_start(rank: int, batch: int) -> int:
@@ -142,6 +193,26 @@ def make_plans(w, prec, torch):
 # full-batch passes of each hot-path kernel in one step (two Zak routes, one FIR route)
 PASSES_PER_STEP = {"zak_fwd": 2, "prod_ifft": 2, "fft_post": 2, "pre_ifft": 2, "fft_prod_adj": 2, "zak_inv": 2,
                    "zak_prod_ifft": 2, "fir_analysis": 1, "fir_synthesis": 1}
+
+
+def flop_model(w, Lg=1024):
+    """Flops per coefficient of each route of the step on the workload's lattice, from the
+    paper's counts: a separable lattice (a, M) costs 4 L log2 d (Zak transform) + 8 L q (block
+    products, p = 1) + 4 M N log2 d + 4 M N log2 M (eq. rect-flops); the coset route runs
+    lambda2 separable lattices (lambda2 a, M); the shear route one separable lattice of the same
+    size; the FIR route 8 L Lg / a + 4 M N log2 M (eq. rect-flops-FIR)."""
+    L, a, M, l2 = w.L, w.a, w.M, w.lam2
+    MN = M * (L // a)
+
+    def sep(at):
+        c = math.gcd(at, M)
+        Nt = L // at
+        d = math.gcd(L // M, Nt)
+        q = M // c
+        MNt = M * Nt
+        return 4 * L * math.log2(d) + 8 * L * q + 4 * MNt * math.log2(d) + 4 * MNt * math.log2(M)
+
+    return {"shear": sep(a) / MN, "coset": l2 * sep(l2 * a) / MN, "fir": (8 * L * Lg / a + 4 * MN * math.log2(M)) / MN}
 
 
 def algorithmic_bytes(name, w, B, csz, rsz, J):
@@ -268,8 +339,17 @@ def run_ours(args, rank, world):
     # several routes in flight at once on separate streams shared the link badly: 3-4x slower).
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     nroutes = len(plans)
-    c_hosts = [torch.empty((B, w.N, w.M), dtype=torch.complex64).pin_memory() for _ in range(nroutes)]
-    fr_hosts = [torch.empty((B, w.L), dtype=torch.float32).pin_memory() for _ in range(nroutes)]
+    # the pinned result buffers are allocated (and so placed) from the CPUs local to the GPU
+    node, cpus = gpu_host_locality(dev.index if dev.index is not None else 0)
+    old_aff = os.sched_getaffinity(0)
+    if cpus:
+        os.sched_setaffinity(0, cpus)
+    try:
+        c_hosts = [torch.empty((B, w.N, w.M), dtype=torch.complex64).pin_memory() for _ in range(nroutes)]
+        fr_hosts = [torch.empty((B, w.L), dtype=torch.float32).pin_memory() for _ in range(nroutes)]
+    finally:
+        os.sched_setaffinity(0, old_aff)
+    host_nodes = page_nodes(c_hosts + fr_hosts + [f_host])
     d2h_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nroutes)]
     cbufs = [cbuf] + [torch.empty_like(cbuf) for _ in range(nroutes - 1)]
     frs = [fr] + [torch.empty_like(fr) for _ in range(nroutes - 1)]
@@ -334,6 +414,26 @@ def run_ours(args, rank, world):
         del plans64, c64, fr64, f64
         torch.cuda.empty_cache()
 
+    # ---------------- arithmetic: measured FMA rates and the paper's flop counts ----------------
+    import ctypes
+
+    rates = {}
+    for kind, name in ((0, "fp32_fma"), (1, "fp32_packed_fma"), (2, "fp64_fma")):
+        v = ctypes.c_double()
+        K.check(K.lib().dgt_fma_rate(kind, ctypes.byref(v), torch.cuda.current_stream(dev).cuda_stream))
+        rates[name + "_tflops"] = v.value / 1e12
+    fp32_peak = max(rates["fp32_fma_tflops"], rates["fp32_packed_fma_tflops"])
+    fpc = flop_model(w)
+    step_flops = 2 * B * w.M * w.N * (fpc["fir"] + fpc["shear"] + fpc["coset"])
+    flops = {"model": "the paper's counts (4 n log2 n per FFT of length n, 8 flops per complex product; eq. "
+                      "rect-flops per separable lattice, the coset route as lambda2 separable lattices, eq. "
+                      "rect-flops-FIR), per coefficient, analysis and synthesis alike",
+             "flop_per_coef": fpc, "flop_per_step": step_flops, "tflops": step_flops / (ms * 1e-3) / 1e12,
+             "measured_peaks": rates, "frac_of_fp32_peak": step_flops / (ms * 1e-3) / 1e12 / fp32_peak}
+    if fp64:
+        fp64["tflops"] = step_flops / (fp64["ms_per_step"] * 1e-3) / 1e12
+        fp64["frac_of_dfma_peak"] = fp64["tflops"] / rates["fp64_fma_tflops"]
+
     # ---------------- roofline of the dominant kernel ----------------
     peak, peak_kind = _peaks()
     kernels = {}
@@ -393,8 +493,12 @@ def run_ours(args, rank, world):
         "gpu_launches": launches * 1 if launches else 0,
         "e2e": {"value": world * coefs_per_step / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "steps": e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "coef_copy_ms_per_route": d2h_ms},
+                "coef_copy_ms_per_route": d2h_ms,
+                "coef_copy_gbs_per_route": [B * w.N * w.M * 8 / (x * 1e-3) / 1e9 if x > 0 else None for x in d2h_ms],
+                "gpu_numa_node": node, "gpu_local_cpus": len(cpus) if cpus else None,
+                "pinned_buffer_numa_nodes": host_nodes},
         "fp64": fp64,
+        "flops": flops,
         "clocks": clk,
         "reconstruction_rel_err": err,
         "serve": serve,
@@ -438,7 +542,9 @@ def run_other_configs(dev, steps=5):
     f64 = signal_batch(w, cfg_id=2)
     g = gaussian_window(w.L)
     res = {}
-    for prec, cdt in (("f32", torch.complex64), ("f64", torch.complex128)):
+    keep = {}
+    half = w.batch // 2
+    for prec, cdt in (("f64", torch.complex128), ("f32", torch.complex64)):
         f = torch.from_numpy(f64.astype(np.complex64 if prec == "f32" else np.complex128)).to(dev)
         c = torch.empty((w.batch, w.N, w.M), dtype=cdt, device=dev)
         fr = torch.empty_like(f)
@@ -452,30 +558,73 @@ def run_other_configs(dev, steps=5):
 
             ms = _time_cuda(step, steps if prec == "f32" else 2)
             err = float(torch.linalg.vector_norm(fr - f) / torch.linalg.vector_norm(f))
-            res["%s_%s" % (route, prec)] = {"ms_per_step": ms, "coef_per_s": 2 * w.batch * w.M * w.N / (ms * 1e-3),
-                                            "reconstruction_rel_err": err}
+            ent = {"ms_per_step": ms, "coef_per_s": 2 * w.batch * w.M * w.N / (ms * 1e-3),
+                   "reconstruction_rel_err": err}
+            if prec == "f64":
+                keep[route] = c.clone()
+            else:
+                # float32 against the float64 path on the same signals (the float64 path matches
+                # the oracle to <= 1e-12 in the tests), per signal, for the noise and chirp halves
+                ref = keep[route]
+                e = (torch.linalg.vector_norm((c.to(torch.complex128) - ref).reshape(w.batch, -1), dim=1)
+                     / torch.linalg.vector_norm(ref.reshape(w.batch, -1), dim=1)).cpu().numpy()
+                ent["rel_l2_vs_f64"] = {"noise_max": float(e[:half].max()), "noise_median": float(np.median(e[:half])),
+                                        "chirp_max": float(e[half:].max()), "chirp_median": float(np.median(e[half:]))}
+            res["%s_%s" % (route, prec)] = ent
             p.close()
         del f, c, fr
-    out["dense_third"] = {"workload": w.name, "batch": w.batch, "step": "analysis + dual synthesis", **res}
+    del keep
+    out["dense_third"] = {"workload": w.name, "batch": w.batch, "step": "analysis + dual synthesis",
+                          "signals": "64 complex N(0,1), then 64 linear chirps 0 -> L/2 with -60 dB noise",
+                          "precision_study": "float32 coefficients against the float64 path's, per signal "
+                                             "(relative l2 over the signal's M x N block)", **res}
     torch.cuda.empty_cache()
     # differentiable: 32 real float32 signals, learnable window, sum log(|c|^2 + 1e-6)
+    from paper_1307_4569_gb300 import log_magnitude_loss
+
     w = DIFFERENTIABLE
     f = torch.from_numpy(np.stack([real_normal(w.L, 5, i) for i in range(w.batch)]).astype(np.float32)).to(dev)
     gw = torch.from_numpy(noisy_gaussian_window(w.L, 5).astype(np.float32)).to(dev)
-    p = Plan(w.L, w.a, w.M, w.lam1, w.lam2, gw.cpu().numpy(), precision="f32")
+    diff = {"workload": w.name, "batch": w.batch,
+            "step": "set the learnable window, analysis, loss sum log(|c|^2 + 1e-6) (fused kernel), backward "
+                    "(signal and window gradients)"}
+    # algorithmic bytes: analysis (real in, complex out), loss (read c, write dl/dc), signal
+    # gradient (read dl/dc, write real), window gradient (read f and dl/dc, write L)
+    nc = w.batch * w.M * w.N
+    diff_bytes = w.batch * w.L * 4 + nc * 8 + 2 * nc * 8 + nc * 8 + w.batch * w.L * 4 + w.batch * w.L * 4 + nc * 8
+    for route in ("coset", "shear"):
+        p = Plan(w.L, w.a, w.M, w.lam1, w.lam2, gw.cpu().numpy(), route=route, precision="f32")
 
-    def train_step():
-        ft = f.requires_grad_(True)
-        gt = gw.detach().clone().requires_grad_(True)
-        cc = dgt_fn(ft, gt, p)
-        loss = torch.log(cc.real ** 2 + cc.imag ** 2 + 1e-6).sum()
-        loss.backward()
+        def train_step():
+            ft = f.requires_grad_(True)
+            gt = gw.detach().clone().requires_grad_(True)
+            loss = log_magnitude_loss(dgt_fn(ft, gt, p), p)
+            loss.backward()
 
-    ms = _time_cuda(train_step, steps)
-    out["differentiable"] = {"workload": w.name, "batch": w.batch, "route": p.route,
-                             "step": "analysis, loss, backward (signal and window gradients)",
-                             "ms_per_step": ms, "coef_per_s": w.batch * w.M * w.N / (ms * 1e-3)}
-    p.close()
+        def eager_step():
+            ft = f.requires_grad_(True)
+            gt = gw.detach().clone().requires_grad_(True)
+            cc = dgt_fn(ft, gt, p)
+            loss = torch.log(cc.real ** 2 + cc.imag ** 2 + 1e-6).sum()
+            loss.backward()
+
+        ms = _time_cuda(train_step, steps)
+        ms_eager = _time_cuda(eager_step, 3)
+        cbuf = torch.empty((w.batch, w.N, w.M), dtype=torch.complex64, device=dev)
+        lv, G = p.logmag_loss(p.dgt(f, out=cbuf))
+        parts = {"set_window_ms": _time_cuda(lambda: p.set_window(gw), steps),
+                 "analysis_ms": _time_cuda(lambda: p.dgt(f, out=cbuf), steps),
+                 "loss_ms": _time_cuda(lambda: p.logmag_loss(cbuf), steps),
+                 "signal_gradient_ms": _time_cuda(lambda: p.idgt(G, window="adjoint", real=True), steps),
+                 "window_gradient_ms": _time_cuda(lambda: p.grad_window(f, G), steps)}
+        diff[route] = {"ms_per_step": ms, "coef_per_s": nc / (ms * 1e-3), "eager_loss_ms_per_step": ms_eager,
+                       "parts": parts, "algorithmic_bytes_per_step": diff_bytes,
+                       "achieved_gbs": diff_bytes / (ms * 1e-3) / 1e9}
+        del cbuf, G, lv
+        p.close()
+    best = min(("coset", "shear"), key=lambda r: diff[r]["ms_per_step"])
+    diff.update({"route": best, "ms_per_step": diff[best]["ms_per_step"], "coef_per_s": diff[best]["coef_per_s"]})
+    out["differentiable"] = diff
     del f, gw
     torch.cuda.empty_cache()
     # blockwise (overlap-add) plans on the audio batch, Hann window of 1024 taps: blocks of
@@ -588,7 +737,7 @@ def run_serve(seconds, rate=2000.0, cap_bytes=40 << 30, seed=4, infeasible_every
     from workloads import serve_requests
 
     reqs = serve_requests(rate, seconds, seed=seed, infeasible_every=infeasible_every)
-    ex = GpuExecutor("f32", streams=4, arena_bytes=cap_bytes // 4)
+    ex = GpuExecutor("f32", streams=4, arena_bytes=cap_bytes // 4, pool=8)
     keys = sorted({request_key(r) for r in reqs if r.feasible})
     t0 = time.time()
     ex.warm(keys)
@@ -607,7 +756,9 @@ def run_serve(seconds, rate=2000.0, cap_bytes=40 << 30, seed=4, infeasible_every
     out.update({"rate_per_s": rate, "seconds": seconds, "cap_bytes": cap_bytes, "plans": len(keys),
                 "plan_warmup_s": warm_s, "redraws": int(sum(r.redraws for r in reqs)),
                 "latency": "result in pinned host memory - scheduled arrival (open loop)",
-                "precision": "f32"})
+                "precision": "f32", "input_pool_per_shape": ex.pool,
+                "accuracy": "float32 results; the serving tests hold every served result within 2e-6 relative "
+                            "l2 of the float64 oracle and bit-identical alone and in the mix"})
     ex.close()
     torch.cuda.synchronize()
     return out
@@ -751,7 +902,7 @@ def main():
     ap.add_argument("--lambda-sweep", action="store_true",
                     help="run only the coset / shear timing sweep over lambda2 = 1..10 (Fig. 2 setups) and "
                          "print its rows as one JSON line")
-    ap.add_argument("--serve-seconds", type=float, default=20.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the serving run (Poisson 2000 requests/s); 0 skips it")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

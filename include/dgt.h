@@ -281,7 +281,13 @@ const char* dgt_last_error(void);
 int dgt_profile_start(void);
 int dgt_profile_stop(char* json, size_t cap);
 
-/* Building block check: `howmany` contiguous complex transforms of length n (device buffers),
+/* Arithmetic throughput probe for roofline statements (no counterpart in the paper): runs
+ * independent fused multiply-add chains on every SM of the current device and returns the
+ * achieved rate in flop/s (2 per FMA per lane): kind 0 scalar float FMA, 1 packed float-pair
+ * FMA, 2 double FMA.  Synchronises `stream`; allocates 4 bytes. */
+int dgt_fma_rate(int kind, double* flops_per_s, void* stream);
+
+/* Building block check: `howmany` contiguous complex transforms of length n (device buffers),/* Building block check: `howmany` contiguous complex transforms of length n (device buffers),
  * direction -1 (forward) or +1 (unnormalised inverse), precision DGT_F32 / DGT_F64. */
 int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, void* out, int64_t howmany,
                      void* stream);

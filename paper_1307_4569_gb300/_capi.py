@@ -78,6 +78,7 @@ SIGNATURES = {
     "dgt_strerror": (C.c_char_p, [i32]),
     "dgt_last_error": (C.c_char_p, []),
     "dgt_fft_selftest": (i32, [i64, i32, i32, vp, vp, i64, vp]),
+    "dgt_fma_rate": (i32, [i32, C.POINTER(C.c_double), vp]),
     "dgt_profile_start": (i32, []),
     "dgt_profile_stop": (i32, [C.c_char_p, C.c_size_t]),
 }

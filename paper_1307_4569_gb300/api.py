@@ -331,3 +331,25 @@ class DGTFunction(torch.autograd.Function):
 
 def dgt(f, g, plan: Plan):
     return DGTFunction.apply(f, g, plan)
+
+
+class LogMagLoss(torch.autograd.Function):
+    """l = sum over the batch and every coefficient of log(|c|^2 + eps), from one pass of the
+    library's kernel that also writes dl/dc = 2 c / (|c|^2 + eps) (the gradient convention
+    d/dRe + i d/dIm); backward scales it by the incoming gradient.  The value is float64."""
+
+    @staticmethod
+    def forward(ctx, c, plan: Plan, eps: float):
+        per_signal, G = plan.logmag_loss(c.detach().contiguous(), eps=eps, need_grad=c.requires_grad)
+        ctx.save_for_backward(G)
+        return per_signal.sum()
+
+    @staticmethod
+    def backward(ctx, grad):
+        (G,) = ctx.saved_tensors
+        return G * grad.to(G.real.dtype), None, None
+
+
+def log_magnitude_loss(c, plan: Plan, eps: float = 1e-6):
+    """sum log(|c|^2 + eps) with the fused forward / gradient kernel (see LogMagLoss)."""
+    return LogMagLoss.apply(c, plan, eps)

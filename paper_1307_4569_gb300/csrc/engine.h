@@ -175,7 +175,7 @@ template <typename T>
 cudaError_t launch_grad_window_combine(const cplx<T>* wj, void* grad, int grad_real, int64_t L, int64_t a, int64_t J,
                                        const int64_t* sigma, const CisTable<cplx<T>>& cisL, cudaStream_t st);
 template <typename T>
-cudaError_t launch_logmag(const cplx<T>* c, cplx<T>* u, double* partial, int64_t n, T eps, int64_t B,
+cudaError_t launch_logmag(const cplx<T>* c, cplx<T>* u, double* partial, double* loss, int64_t n, T eps, int64_t B,
                           cudaStream_t st);
 
 // dual / tight window Gram blocks (float64)
@@ -212,6 +212,9 @@ cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, 
 // cycles that launches pass to the kernels (a test hook lowers it).  A CTA whose wait expires
 // sets the caller's word `expired` to 1 (a plan's host-mapped word, or the word at the start
 // of a caller workspace), so each expiry is traced to the plan or workspace of its launch.
+// arithmetic throughput probe: kind 0 scalar float FMA, 1 packed float pairs, 2 double FMA;
+// `blocks` CTAs of 256 threads, 8 chains of `iters` FMAs per thread; flop/s (2 per FMA lane)
+cudaError_t fma_rate(int kind, int iters, int blocks, float* out, cudaStream_t st, double* flops);
 constexpr long long kWaitCycles = 2000000000LL;       // about a second
 extern long long g_wait_limit_cycles;
 // columns per chunk of the power-of-two FIR synthesis for FFT length M (0: not applicable)

@@ -310,14 +310,24 @@ __global__ void logmag_kernel(const cplx<T>* __restrict__ c, cplx<T>* __restrict
                               int64_t n, T eps) {
     __shared__ double red[256];
     const int64_t b = blockIdx.y;
-    double acc = 0;
+    // float: single-precision logarithms summed with a compensated (Kahan) float sum per thread,
+    // then a float64 tree over the CTA; float64: the float64 logarithm and sum
+    T acc = 0, comp = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const cplx<T> v = c[b * n + e];
         const T m2 = v.x * v.x + v.y * v.y + eps;
-        acc += log((double)m2);
-        if (u) u[b * n + e] = cscale(v, (T)2 / m2);
+        const T y = log(m2) - comp;
+        const T s = acc + y;
+        comp = (s - acc) - y;
+        acc = s;
+        if (u) {
+            T inv;
+            if constexpr (sizeof(T) == 4) inv = __fdividef(2.f, m2);
+            else inv = (T)2 / m2;
+            u[b * n + e] = cscale(v, inv);
+        }
     }
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = (double)acc;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -326,11 +336,27 @@ __global__ void logmag_kernel(const cplx<T>* __restrict__ c, cplx<T>* __restrict
     if (threadIdx.x == 0) partial[b * gridDim.x + blockIdx.x] = red[0];
 }
 
+// loss_b = sum of the P partial sums of signal b (float64)
+__global__ void logmag_finish_kernel(const double* __restrict__ partial, double* __restrict__ loss, int P) {
+    __shared__ double red[64];
+    const int64_t b = blockIdx.x;
+    red[threadIdx.x] = threadIdx.x < P ? partial[b * P + threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int s = 32; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss[b] = red[0];
+}
+
 template <typename T>
-cudaError_t launch_logmag(const cplx<T>* c, cplx<T>* u, double* partial, int64_t n, T eps, int64_t B,
+cudaError_t launch_logmag(const cplx<T>* c, cplx<T>* u, double* partial, double* loss, int64_t n, T eps, int64_t B,
                           cudaStream_t st) {
-    dim3 grid(64, (unsigned)B);
-    logmag_kernel<T><<<grid, 256, 0, st>>>(c, u, partial, n, eps);
+    constexpr int P = 64;
+    logmag_kernel<T><<<dim3(P, (unsigned)B), 256, 0, st>>>(c, u, partial, n, eps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    logmag_finish_kernel<<<(unsigned)B, 64, 0, st>>>(partial, loss, P);
     return cudaGetLastError();
 }
 
@@ -762,6 +788,84 @@ cudaError_t noalloc_scratch(void** out) {
     return cudaSuccess;
 }
 
+// =====================================================================================
+// Arithmetic throughput probe: every thread runs 8 independent fused multiply-add chains
+// (scalar float, packed float pairs or double) for `iters` steps; the result is stored only
+// when it equals a value no chain reaches, so the chains are not removed.
+// =====================================================================================
+template <int KIND>
+__global__ void __launch_bounds__(256) fma_rate_kernel(int iters, float seed, float* out) {
+    constexpr int K = 8;
+    if constexpr (KIND == 0) {
+        float a[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) a[i] = seed + (float)(threadIdx.x + i);
+        const float x = 0.999f, y = 1e-3f;
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int i = 0; i < K; ++i) a[i] = fmaf(a[i], x, y);
+        float sacc = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) sacc += a[i];
+        if (sacc == -1.f) out[0] = sacc;
+    } else if constexpr (KIND == 1) {
+        float2 a[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) a[i] = make_float2(seed + (float)(threadIdx.x + i), seed - (float)i);
+        const float2 x = make_float2(0.999f, 0.998f), y = make_float2(1e-3f, 2e-3f);
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int i = 0; i < K; ++i) a[i] = __ffma2_rn(a[i], x, y);
+        float sacc = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) sacc += a[i].x + a[i].y;
+        if (sacc == -1.f) out[0] = sacc;
+    } else {
+        double a[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) a[i] = (double)seed + (double)(threadIdx.x + i);
+        const double x = 0.999, y = 1e-3;
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int i = 0; i < K; ++i) a[i] = fma(a[i], x, y);
+        double sacc = 0.0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) sacc += a[i];
+        if (sacc == -1.0) out[0] = (float)sacc;
+    }
+}
+
+cudaError_t fma_rate(int kind, int iters, int blocks, float* out, cudaStream_t st, double* flops) {
+    constexpr int K = 8, THR = 256;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    auto launch = [&](int n) {
+        if (kind == 0) fma_rate_kernel<0><<<blocks, THR, 0, st>>>(n, 1.f, out);
+        else if (kind == 1) fma_rate_kernel<1><<<blocks, THR, 0, st>>>(n, 1.f, out);
+        else fma_rate_kernel<2><<<blocks, THR, 0, st>>>(n, 1.f, out);
+    };
+    launch(iters / 8);                                      // warm-up
+    cudaEventRecord(e0, st);
+    launch(iters);
+    cudaEventRecord(e1, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    const double fmas = (double)blocks * THR * K * (double)iters * (kind == 1 ? 2.0 : 1.0);
+    *flops = 2.0 * fmas / (ms * 1e-3);
+    return cudaSuccess;
+}
+
 #define DGT_INST_AUX(T)                                                                                               \
     template cudaError_t launch_fir_analysis<T>(const void*, int, cplx<T>*, const FirParams<cplx<T>>&, const FftRef&, \
                                                 int64_t, cudaStream_t);                                               \
@@ -771,7 +875,7 @@ cudaError_t noalloc_scratch(void** out) {
                                                  const int64_t*, const CisTable<cplx<T>>&, cudaStream_t);             \
     template cudaError_t launch_grad_window_combine<T>(const cplx<T>*, void*, int, int64_t, int64_t, int64_t,         \
                                                        const int64_t*, const CisTable<cplx<T>>&, cudaStream_t);       \
-    template cudaError_t launch_logmag<T>(const cplx<T>*, cplx<T>*, double*, int64_t, T, int64_t, cudaStream_t);
+    template cudaError_t launch_logmag<T>(const cplx<T>*, cplx<T>*, double*, double*, int64_t, T, int64_t, cudaStream_t);
 
 DGT_INST_AUX(float)
 DGT_INST_AUX(double)

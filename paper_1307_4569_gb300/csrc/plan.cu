@@ -423,6 +423,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     DevBuf firmt[4];                   // FIR route: modulated taps [lam2][Lg] of the windows in gam / gT
     DevBuf lossparts;
     DevBuf hbtab;                      // FIR route, lambda2 = 2: exp(-pi i k / M), k < M (real-input pairing)
+    DevBuf gradws;                     // work arrays of the window gradient
 
     const FftRef* fft(int64_t n) {
         auto it = tw.find(n);
@@ -477,7 +478,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     size_t ws_bytes(int64_t B) const override { return layout(B).total; }
     size_t owned_bytes() const override {
         size_t s = sigma.bytes + g64.bytes + gT.bytes + work.bytes + tmpwin.bytes + status.bytes + lossparts.bytes +
-                   real_full.bytes + hbtab.bytes;
+                   real_full.bytes + hbtab.bytes + gradws.bytes;
         for (int i = 0; i < 4; ++i) s += zg[i].bytes + gam[i].bytes + firmt[i].bytes;
         for (auto& kv : tw) s += kv.second->buf.bytes;
         s += cisL.hi.bytes + cisL.lo.bytes + cis2L.hi.bytes + cis2L.lo.bytes + cis2N.hi.bytes + cis2N.lo.bytes +
@@ -906,9 +907,8 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         pp.mb = make_mod((uint64_t)k.b);
         const size_t need = al(sizeof(C) * (size_t)B * k.L) + al(sizeof(C) * (size_t)B * k.M * k.N) +
                             2 * al(sizeof(C) * (size_t)k.lam2 * k.L);
-        DevBuf scratch;
-        DGT_TRY(scratch.alloc(need));
-        char* p = (char*)scratch.p;
+        DGT_TRY(gradws.alloc(need));               // plan-owned, grown on demand
+        char* p = (char*)gradws.p;
         C* zf = (C*)p; p += al(sizeof(C) * (size_t)B * k.L);
         C* y = (C*)p; p += al(sizeof(C) * (size_t)B * k.M * k.N);
         C* v = (C*)p; p += al(sizeof(C) * (size_t)k.lam2 * k.L);
@@ -919,7 +919,6 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         KTRY("zak_inv", st, launch_zak_inv<T>(v, k.L, wj, 0, k.L, k.L, cg.d, *fd, nochirp(), (T)1, k.lam2, st));
         KTRY("grad_window_combine", st, launch_grad_window_combine<T>(wj, grad, grad_real, k.L, k.a, k.lam2, (const int64_t*)sigma.p,
                                                cisL.tab, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
         return DGT_OK;
     }
 
@@ -973,15 +972,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) override {
         const PlanCore& k = core;
         DGT_TRY(lossparts.alloc(sizeof(double) * 64 * B));
-        KTRY("logmag", st, launch_logmag<T>((const C*)c, (C*)G, (double*)lossparts.p, k.M * k.N, (T)eps, B, st));
-        std::vector<double> h(64 * B);
-        CUDA_TRY(cudaMemcpyAsync(h.data(), lossparts.p, sizeof(double) * 64 * B, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
-        std::vector<double> out(B, 0.0);
-        for (int64_t b = 0; b < B; ++b)
-            for (int i = 0; i < 64; ++i) out[b] += h[b * 64 + i];
-        CUDA_TRY(cudaMemcpyAsync(loss, out.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
+        KTRY("logmag", st, launch_logmag<T>((const C*)c, (C*)G, (double*)lossparts.p, loss, k.M * k.N, (T)eps, B, st));
         return DGT_OK;
     }
 };
@@ -1642,6 +1633,19 @@ int dgt_profile_stop(char* json, size_t cap) {
         json[cap - 1] = 0;
         if (out.size() >= cap) return fail(DGT_ERR_ARG, "profile buffer too small (%zu bytes needed)", out.size() + 1);
     }
+    return DGT_OK;
+}
+
+int dgt_fma_rate(int kind, double* flops_per_s, void* stream) {
+    if (!flops_per_s || kind < 0 || kind > 2) return fail(DGT_ERR_ARG, "bad argument");
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DevBuf sink;
+    DGT_TRY(sink.alloc(sizeof(float)));
+    // 8 resident CTAs of 256 threads per SM; about 10 ms of float work
+    const int iters = kind == 2 ? 1 << 12 : 1 << 16;
+    CUDA_TRY(fma_rate(kind, iters, 8 * sms, (float*)sink.p, (cudaStream_t)stream, flops_per_s));
     return DGT_OK;
 }
 

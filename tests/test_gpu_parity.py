@@ -238,6 +238,16 @@ def test_gradients_subcase(prec):
     # library loss helper agrees
     lv, G = p.logmag_loss(c.detach())
     assert abs(lv.sum().item() - ref_l) <= (1e-10 if prec == "f64" else 1e-4) * abs(ref_l)
+    # the fused loss as an autograd function: same value and gradients
+    from paper_1307_4569_gb300 import log_magnitude_loss
+
+    ft2 = _to_dev(_round(f, prec), prec).requires_grad_(True)
+    gt2 = _to_dev(_round(g, prec), prec).requires_grad_(True)
+    loss2 = log_magnitude_loss(dgt_fn(ft2, gt2, p), p)
+    loss2.backward()
+    assert abs(loss2.item() - ref_l) <= (1e-10 if prec == "f64" else 1e-4) * abs(ref_l)
+    assert _rel(ft2.grad.cpu().numpy(), ref_gf) <= tol
+    assert _rel(gt2.grad.cpu().numpy(), ref_gg) <= tol
 
 
 def _gradient_response(f, g, a, M, l1, l2, rel, trials=2):
