@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "lib", "obj")
 LIB = os.path.join(LIBDIR, "libdgt.so")
 SOURCES = ["engine_zak.cu", "engine_aux.cu", "plan.cu", "p2_cols_f32.cu", "p2_rows_f32.cu", "p2_cols_f64.cu",
-           "p2_rows_f64.cu"]
+           "p2_rows_f64.cu", "mr_f32.cu", "mr_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

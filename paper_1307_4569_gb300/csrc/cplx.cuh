@@ -108,6 +108,33 @@ inline ModU64 make_mod(uint64_t d) {
     return r;
 }
 
+// 32-bit form for arguments below 2^32: quotient estimate floor(x m / 2^32) with
+// m = floor((2^32 - 1) / d), which is short by at most two (two corrections)
+struct ModU32 {
+    uint32_t d;
+    uint32_t m;
+    __device__ __forceinline__ uint32_t div(uint32_t x) const {
+        uint32_t q = __umulhi(x, m);
+        uint32_t r = x - q * d;
+        if (r >= d) { r -= d; ++q; }
+        if (r >= d) ++q;
+        return q;
+    }
+    __device__ __forceinline__ uint32_t mod(uint32_t x) const {
+        const uint32_t q = __umulhi(x, m);
+        uint32_t r = x - q * d;
+        if (r >= d) r -= d;
+        if (r >= d) r -= d;
+        return r;
+    }
+};
+inline ModU32 make_mod32(uint32_t d) {
+    ModU32 r;
+    r.d = d;
+    r.m = 0xffffffffu / d;
+    return r;
+}
+
 // exp(2 pi i e / den) for integer e (any sign), from a two-level table built on the
 // host in double precision: hi[k] = exp(2 pi i k S / den), lo[r] = exp(2 pi i r / den),
 // e mod den = k S + r with S a power of two.  Two rounded factors, so the result is

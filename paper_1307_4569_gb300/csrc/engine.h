@@ -48,6 +48,11 @@ template <typename C> struct PostParams {
     ModU64 mJN, mNs;                  // row = (b J + j) Ns + n of Y: division by J Ns and Ns (set by the launchers)
     int64_t lam1;                     // w(n) of the output columns (real-signal coefficients)
     int half;                         // coefficients hold channels 0..M/2 only (real signals, lam2 <= 2)
+    // shear1 in 32-bit arithmetic (host-checked: (2N)^2 and L Nr below 2^32): the constants
+    // above reduced to 32 bits and the reductions modulo 2N, L and the division by b
+    int sh1_fast;
+    uint32_t f_Nr, f_N, f_M, f_C1, f_C2, f_C3, f_C4, f_C5, f_s1ar, f_C6;
+    ModU32 q2N, qL, qb;
 };
 
 // Signal pre-processing inside the factorisation / FFT_L passes.
@@ -96,9 +101,11 @@ cudaError_t launch_zak_inv(const cplx<T>* zf, int64_t zf_bstride, void* dst, int
                            int64_t B, cudaStream_t st);
 
 // window gradient through the factorisation: V_j[xi][col] accumulated over the batch
+// (part: scratch of fft_grad_window_groups() J L elements for the per-group sums, or null for one group)
 template <typename T>
-cudaError_t launch_fft_grad_window(const cplx<T>* y, const cplx<T>* zf, int64_t J, cplx<T>* v, const SepGeom& g,
-                                   const FftRef& fd, int64_t B, cudaStream_t st);
+cudaError_t launch_fft_grad_window(const cplx<T>* y, const cplx<T>* zf, int64_t J, cplx<T>* v, cplx<T>* part,
+                                   const SepGeom& g, const FftRef& fd, int64_t B, cudaStream_t st);
+int64_t fft_grad_window_groups(const SepGeom& g, int64_t J, int64_t B, size_t elem);
 
 // four-step FFT of length L = L1 * L2 (frequency-shear branch and window set-up)
 template <typename T>
@@ -207,6 +214,26 @@ cudaError_t p2_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx
                             const void* tw, int64_t B, unsigned int* expired, cudaStream_t st);
 template <typename T>
 cudaError_t p2_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
+                       const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
+// mixed-radix row kernels (kernels_mr.cuh): cudaErrorNotSupported for a length without a
+// compiled transform
+template <typename T>
+cudaError_t mr_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const void* tw,
+                        const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t mr_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const void* tw,
+                        const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t mr_zak_fwd(const void* src, int src_real, int64_t sbs, cplx<T>* zf, int64_t zbs, int64_t d, int64_t K0,
+                       const void* tw, const ChirpParams<cplx<T>>& pre, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t mr_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T>* y, const SepGeom& g,
+                         const void* tw, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t mr_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
+                            const void* tw, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t mr_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
                        const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
 // Bounded device waits (the tensor-copy staging of fft_prod_adj): the wait limit in clock
 // cycles that launches pass to the kernels (a test hook lowers it).  A CTA whose wait expires

@@ -73,7 +73,9 @@ template <typename T>
 cudaError_t launch_zak_fwd(const void* src, int src_real, int64_t sbs, cplx<T>* zf, int64_t zbs, int64_t L, int64_t d,
                            const FftRef& fd, const ChirpParams<cplx<T>>& pre, int64_t B, cudaStream_t st) {
     {
-        const cudaError_t e = p2_zak_fwd<T>(src, src_real, sbs, zf, zbs, d, L / d, fd.tw, pre, B, st);
+        cudaError_t e = p2_zak_fwd<T>(src, src_real, sbs, zf, zbs, d, L / d, fd.tw, pre, B, st);
+        if (e != cudaErrorNotSupported) return e;
+        e = mr_zak_fwd<T>(src, src_real, sbs, zf, zbs, d, L / d, fd.tw, pre, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
     using C = cplx<T>;
@@ -142,7 +144,9 @@ template <typename T>
 cudaError_t launch_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T>* y, const SepGeom& g,
                              const FftRef& fd, int64_t B, cudaStream_t st) {
     {
-        const cudaError_t e = p2_prod_ifft<T>(zf, zg, J, y, g, fd.tw, B, st);
+        cudaError_t e = p2_prod_ifft<T>(zf, zg, J, y, g, fd.tw, B, st);
+        if (e != cudaErrorNotSupported) return e;
+        e = mr_prod_ifft<T>(zf, zg, J, y, g, fd.tw, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
     using C = cplx<T>;
@@ -219,7 +223,9 @@ template <typename T>
 cudaError_t launch_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const FftRef& fm,
                             const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
     {
-        const cudaError_t e = p2_fft_post<T>(y, c, g, J, fm.tw, pp, B, st);
+        cudaError_t e = p2_fft_post<T>(y, c, g, J, fm.tw, pp, B, st);
+        if (e != cudaErrorNotSupported) return e;
+        e = mr_fft_post<T>(y, c, g, J, fm.tw, pp, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
     if (pp.half) return cudaErrorNotSupported;       // half-channel output: power-of-two kernels only
@@ -295,7 +301,9 @@ template <typename T>
 cudaError_t launch_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const FftRef& fm,
                             const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
     {
-        const cudaError_t e = p2_pre_ifft<T>(c, y, g, J, fm.tw, pp, B, st);
+        cudaError_t e = p2_pre_ifft<T>(c, y, g, J, fm.tw, pp, B, st);
+        if (e != cudaErrorNotSupported) return e;
+        e = mr_pre_ifft<T>(c, y, g, J, fm.tw, pp, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
     if (pp.half) return cudaErrorNotSupported;
@@ -376,7 +384,9 @@ template <typename T>
 cudaError_t launch_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
                                 const FftRef& fd, int64_t B, unsigned int* expired, cudaStream_t st) {
     {
-        const cudaError_t e = p2_fft_prod_adj<T>(y, zg, J, zf, g, fd.tw, B, expired, st);
+        cudaError_t e = p2_fft_prod_adj<T>(y, zg, J, zf, g, fd.tw, B, expired, st);
+        if (e != cudaErrorNotSupported) return e;
+        e = mr_fft_prod_adj<T>(y, zg, J, zf, g, fd.tw, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
     using C = cplx<T>;
@@ -403,7 +413,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreadsBig) fft_grad_window_kernel(const cplx<T>* __restrict__ y,
                                                                       const cplx<T>* __restrict__ zf,
                                                                       cplx<T>* __restrict__ v, SepGeom g, int64_t J,
-                                                                      int64_t B, int W, FftPlanDev pl,
+                                                                      int64_t B, int64_t Bper, int W, FftPlanDev pl,
                                                                       const cplx<T>* __restrict__ tw) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -417,7 +427,9 @@ __global__ void __launch_bounds__(kThreadsBig) fft_grad_window_kernel(const cplx
     const int64_t Nsep = g.d * g.q;
     const T scale = (T)1 / (T)g.d;
     for (int e = threadIdx.x; e < total; e += blockDim.x) acc[e] = mk((T)0, (T)0);
-    for (int64_t b = 0; b < B; ++b) {
+    // signals [b0, b1) of this CTA's batch group; group z's sums go to v + z J L
+    const int64_t b0 = (int64_t)blockIdx.z * Bper, b1 = min(B, b0 + Bper);
+    for (int64_t b = b0; b < b1; ++b) {
         const C* yb = y + ((b * J + j) * Nsep) * g.M;
         const C* zfb = zf + b * g.L;
         for (int64_t w = 0; w < g.q; ++w) {
@@ -442,27 +454,53 @@ __global__ void __launch_bounds__(kThreadsBig) fft_grad_window_kernel(const cplx
         }
     }
     __syncthreads();
-    C* vj = v + j * g.L;
+    C* vj = v + ((int64_t)blockIdx.z * J + j) * g.L;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int xi = e / nbc, cc = e % nbc;
         vj[xi * g.K0 + col0 + cc] = acc[e];
     }
 }
 
+// v[e] = sum over the batch groups z of part[z n + e] (fixed order: deterministic)
 template <typename T>
-cudaError_t launch_fft_grad_window(const cplx<T>* y, const cplx<T>* zf, int64_t J, cplx<T>* v, const SepGeom& g,
-                                   const FftRef& fd, int64_t B, cudaStream_t st) {
+__global__ void sum_groups_kernel(const cplx<T>* __restrict__ part, cplx<T>* __restrict__ v, int64_t n, int groups) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        cplx<T> s = part[e];
+        for (int z = 1; z < groups; ++z) s = cadd(s, part[z * n + e]);
+        v[e] = s;
+    }
+}
+
+int64_t fft_grad_window_groups(const SepGeom& g, int64_t J, int64_t B, size_t elem) {
+    const int64_t elems = (int64_t)(kSmemBudget / elem);
+    const int64_t W = std::min<int64_t>({elems / (3 * g.d), 16, g.K0});
+    if (W < 1) return 1;
+    const int64_t ctas = (g.K0 + W - 1) / W * J;
+    // about eight CTAs per SM of a 152-SM device
+    return std::max<int64_t>(1, std::min<int64_t>(B, (1216 + ctas - 1) / ctas));
+}
+
+template <typename T>
+cudaError_t launch_fft_grad_window(const cplx<T>* y, const cplx<T>* zf, int64_t J, cplx<T>* v, cplx<T>* part,
+                                   const SepGeom& g, const FftRef& fd, int64_t B, cudaStream_t st) {
     using C = cplx<T>;
     const int64_t elems = (int64_t)(kSmemBudget / sizeof(C));
     const int64_t W = std::min<int64_t>({elems / (3 * g.d), 16, g.K0});
     if (W < 1) return cudaErrorInvalidValue;
+    const int64_t groups = part ? fft_grad_window_groups(g, J, B, sizeof(C)) : 1;
+    const int64_t Bper = (B + groups - 1) / groups;
+    const int64_t used = (B + Bper - 1) / Bper;               // groups that hold signals
     const int thr = threads_for(g.d * W);
     const size_t smem = sizeof(C) * (size_t)g.d * W * 3;
     auto k = fft_grad_window_kernel<T>;
     cudaError_t e = prep_smem(k, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((g.K0 + W - 1) / W), (unsigned)J);
-    k<<<grid, thr, smem, st>>>(y, zf, v, g, J, B, (int)W, fd.pl, (const C*)fd.tw);
+    dim3 grid((unsigned)((g.K0 + W - 1) / W), (unsigned)J, (unsigned)used);
+    k<<<grid, thr, smem, st>>>(y, zf, used > 1 ? part : v, g, J, B, Bper, (int)W, fd.pl, (const C*)fd.tw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || used <= 1) return e;
+    const int64_t n = J * g.L;
+    sum_groups_kernel<T><<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(part, v, n, (int)used);
     return cudaGetLastError();
 }
 
@@ -501,7 +539,9 @@ template <typename T>
 cudaError_t launch_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t L, int64_t d,
                            const FftRef& fd, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st) {
     {
-        const cudaError_t e = p2_zak_inv<T>(zf, zbs, dst, dst_real, dbs, d, L / d, fd.tw, post, scale, B, st);
+        cudaError_t e = p2_zak_inv<T>(zf, zbs, dst, dst_real, dbs, d, L / d, fd.tw, post, scale, B, st);
+        if (e != cudaErrorNotSupported) return e;
+        e = mr_zak_inv<T>(zf, zbs, dst, dst_real, dbs, d, L / d, fd.tw, post, scale, B, st);
         if (e != cudaErrorNotSupported) return e;
     }
     using C = cplx<T>;
@@ -679,7 +719,7 @@ cudaError_t launch_fft_rows_test(const cplx<T>* in, cplx<T>* out, const FftRef& 
                                             const PostParams<cplx<T>>&, int64_t, cudaStream_t);                       \
     template cudaError_t launch_fft_prod_adj<T>(const cplx<T>*, const cplx<T>*, int64_t, cplx<T>*, const SepGeom&,    \
                                                 const FftRef&, int64_t, unsigned int*, cudaStream_t);                 \
-    template cudaError_t launch_fft_grad_window<T>(const cplx<T>*, const cplx<T>*, int64_t, cplx<T>*,                 \
+    template cudaError_t launch_fft_grad_window<T>(const cplx<T>*, const cplx<T>*, int64_t, cplx<T>*, cplx<T>*,       \
                                                    const SepGeom&, const FftRef&, int64_t, cudaStream_t);             \
     template cudaError_t launch_zak_inv<T>(const cplx<T>*, int64_t, void*, int, int64_t, int64_t, int64_t,            \
                                            const FftRef&, const ChirpParams<cplx<T>>&, T, int64_t, cudaStream_t);     \

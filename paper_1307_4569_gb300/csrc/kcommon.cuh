@@ -76,4 +76,38 @@ __device__ __forceinline__ int64_t out_index(const PostParams<C>& pp, const SepG
     }
 }
 
+// The frequency-shear map (POST_SHEAR1) of one row in 32-bit arithmetic: the terms that
+// depend on the separable time index n alone are formed once per row, the rest per channel.
+// Same values as out_index (sh1_fast rows only).
+struct Sh1Row {
+    uint32_t A;        // C2 n mod 2N
+    uint32_t Bq;       // C4 n mod 2N
+    uint32_t Kc;       // C6 n mod L
+    uint32_t n2;       // n mod 2N
+    int64_t base;      // b N M
+};
+template <typename C> __device__ __forceinline__ Sh1Row sh1_row(const PostParams<C>& pp, int64_t b, int64_t n) {
+    Sh1Row r;
+    r.n2 = pp.q2N.mod((uint32_t)n);
+    r.A = pp.q2N.mod(pp.f_C2 * r.n2);
+    r.Bq = pp.q2N.mod(pp.f_C4 * r.n2);
+    r.Kc = pp.qL.mod((uint32_t)((uint64_t)pp.f_C6 * (uint32_t)n % pp.qL.d));
+    r.base = b * pp.N * pp.M;
+    return r;
+}
+template <typename C>
+__device__ __forceinline__ int64_t sh1_at(const PostParams<C>& pp, const Sh1Row& r, int m, C& ph) {
+    const uint32_t twoN = pp.q2N.d;
+    const uint32_t k = m ? pp.f_Nr - (uint32_t)m : 0u;           // -kappa mod Nr
+    const uint32_t k2 = pp.q2N.mod(k);
+    const uint32_t sq1 = pp.q2N.mod(pp.f_C1 * k2 + r.A);
+    const uint32_t mt = sq1 >= pp.f_N ? sq1 - pp.f_N : sq1;
+    const uint32_t t1 = pp.q2N.mod(pp.f_C3 * pp.q2N.mod(sq1 * sq1));
+    const uint32_t inner = pp.q2N.mod(r.Bq + pp.f_C5 * k2);
+    const uint32_t t2 = pp.q2N.mod(r.n2 * inner);
+    ph = pp.cis2N.at(t1 >= t2 ? t1 - t2 : t1 + twoN - t2);
+    const uint32_t kt = pp.qb.div(pp.qL.mod(pp.f_s1ar * pp.qL.mod(k) + r.Kc));
+    return r.base + (int64_t)mt * pp.M + kt;
+}
+
 }  // namespace dgt

@@ -1,0 +1,385 @@
+// Hot-path kernels for mixed-radix FFT lengths (fft_mr): the channel FFT with the route's
+// post-processing (fft_post) and its adjoint (pre_ifft), for the lengths listed in MR_SWITCH;
+// the same arithmetic as the power-of-two row kernels of kernels_p2.cuh, with the transform
+// of fft_mr.cuh and indices reduced modulo N by comparison instead of masks.
+#pragma once
+#include "fft_mr.cuh"
+#include "kernels_p2.cuh"
+
+namespace dgt {
+
+// rows per CTA: about 256 threads
+template <class F> struct MrRow {
+    static constexpr int RPB = F::G >= 256 ? 1 : 256 / F::G;
+    static constexpr int THREADS = RPB * F::G;
+};
+
+template <int N> __device__ __forceinline__ int wrapn(int x) { return x >= N ? x - N : x; }
+
+template <typename T, class F, bool SH1>
+__global__ void __launch_bounds__(MrRow<F>::THREADS) fft_post_mr(const cplx<T>* __restrict__ y, cplx<T>* __restrict__ c,
+                                                                 SepGeom g, int64_t J, int64_t rows_total,
+                                                                 const cplx<T>* __restrict__ tw, PostParams<cplx<T>> pp) {
+    using C = cplx<T>;
+    constexpr int N = F::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / F::G, t = threadIdx.x % F::G;
+    C* sm = reinterpret_cast<C*>(smem_raw) + gi * F::SMEM;
+    const int64_t row = (int64_t)blockIdx.x * MrRow<F>::RPB + gi;
+    const bool ok = row < rows_total;
+    const C* yr = y + row * N;
+    const int64_t b = ok ? (int64_t)pp.mJN.div((uint64_t)row) : 0;
+    const int64_t rem = row - b * (int64_t)pp.mJN.d;
+    const int64_t j = ok ? (int64_t)pp.mNs.div((uint64_t)rem) : 0, nn = ok ? rem - j * (int64_t)pp.mNs.d : 0;
+    C v[F::V];
+    if constexpr (SH1) {
+        fft_mr<F, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
+        if (!ok) return;
+        if (pp.sh1_fast) {
+            const Sh1Row sr = sh1_row(pp, b, nn);
+#pragma unroll
+            for (int i = 0; i < F::OUT; ++i) {
+                if (!mr_out_ok<F>(t, i)) continue;
+                C ph;
+                const int64_t o = sh1_at(pp, sr, mr_out_pos<F>(t, i), ph);
+                c[o] = cmul(v[i], ph);
+            }
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < F::OUT; ++i) {
+            if (!mr_out_ok<F>(t, i)) continue;
+            C ph;
+            const int64_t o = out_index(pp, g, b, j, nn, mr_out_pos<F>(t, i), ph);
+            c[o] = cmul(v[i], ph);
+        }
+    } else {
+        RowMap<C> rm{};
+        if (ok) rm = row_map(pp, g, b, j, nn);
+        fft_mr<F, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
+        if (!ok) return;
+        const int rot = (int)rm.rot;
+        C* cb = c + rm.base;
+#pragma unroll
+        for (int i = 0; i < F::OUT; ++i)
+            if (mr_out_ok<F>(t, i)) cb[wrapn<N>(mr_out_pos<F>(t, i) + rot)] = cmul(v[i], rm.ph);
+    }
+}
+
+template <typename T, class F, bool SH1>
+__global__ void __launch_bounds__(MrRow<F>::THREADS) pre_ifft_mr(const cplx<T>* __restrict__ c, cplx<T>* __restrict__ y,
+                                                                 SepGeom g, int64_t J, int64_t rows_total,
+                                                                 const cplx<T>* __restrict__ tw, PostParams<cplx<T>> pp) {
+    using C = cplx<T>;
+    constexpr int N = F::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / F::G, t = threadIdx.x % F::G;
+    C* sm = reinterpret_cast<C*>(smem_raw) + gi * F::SMEM;
+    const int64_t row = (int64_t)blockIdx.x * MrRow<F>::RPB + gi;
+    const bool ok = row < rows_total;
+    const int64_t b = ok ? (int64_t)pp.mJN.div((uint64_t)row) : 0;
+    const int64_t rem = row - b * (int64_t)pp.mJN.d;
+    const int64_t j = ok ? (int64_t)pp.mNs.div((uint64_t)rem) : 0, nn = ok ? rem - j * (int64_t)pp.mNs.d : 0;
+    C v[F::V];
+    if constexpr (SH1) {
+        if (pp.sh1_fast) {
+            const Sh1Row sr = sh1_row(pp, b, nn);
+            fft_mr<F, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                if (!ok) return mk((T)0, (T)0);
+                C ph;
+                const int64_t o = sh1_at(pp, sr, m, ph);
+                return cmulc(c[o], ph);
+            }, v);
+        } else {
+            fft_mr<F, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                if (!ok) return mk((T)0, (T)0);
+                C ph;
+                const int64_t o = out_index(pp, g, b, j, nn, m, ph);
+                return cmulc(c[o], ph);
+            }, v);
+        }
+    } else {
+        RowMap<C> rm{};
+        if (ok) rm = row_map(pp, g, b, j, nn);
+        const int rot = (int)rm.rot;
+        const C* cb = c + (ok ? rm.base : 0);
+        fft_mr<F, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+            return ok ? cmulc(cb[wrapn<N>(m + rot)], rm.ph) : mk((T)0, (T)0);
+        }, v);
+    }
+    if (!ok) return;
+    C* yr = y + row * N;
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i)
+        if (mr_out_ok<F>(t, i)) yr[mr_out_pos<F>(t, i)] = v[i];
+}
+
+// ------------------------------------------------------------------------------------
+// column kernels (transforms along the strided dimension, W adjacent columns per CTA): the
+// Zak transform, the block product with the inverse FFT over xi, its adjoint, and the inverse
+// Zak transform -- the arithmetic of zak_fwd_p2, prod_ifft_p2, fft_prod_adj_p2, zak_inv_p2
+// ------------------------------------------------------------------------------------
+template <typename T, class F> struct MrCol {
+    static constexpr int WMAX = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int WT = 512 / F::G < 1 ? 1 : 512 / F::G;
+    static constexpr int W = WMAX < WT ? WMAX : WT;
+    static constexpr int THREADS = W * F::G;
+    static constexpr size_t SMEM = sizeof(cplx<T>) * (size_t)F::SMEM * W;
+    // the adjoint holds its accumulators beside the transform: at most 128 registers a thread
+    static constexpr int MINB_ADJ = 65536 / (THREADS * 128) > 0 ? 65536 / (THREADS * 128) : 1;
+};
+
+template <typename T, class F>
+__global__ void __launch_bounds__(MrCol<T, F>::THREADS) zak_fwd_mr(const void* __restrict__ src, int src_real,
+                                                                   int64_t sbs, cplx<T>* __restrict__ zf, int64_t zbs,
+                                                                   int64_t K0, const cplx<T>* __restrict__ tw,
+                                                                   ChirpParams<cplx<T>> pre) {
+    using C = cplx<T>;
+    using CF = MrCol<T, F>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.y;
+    const int64_t col = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = col < K0;
+    C v[F::V];
+    fft_mr<F, -1, CF::W>(c, t, sm, tw, [&](int e) -> C {
+        if (!ok) return mk((T)0, (T)0);
+        const int64_t l = col + K0 * e;
+        C x = load_any<C>(src, src_real, b * sbs + l);
+        if (pre.mode == PRE_CHIRP) x = cmul(x, chirp_factor(pre, l));
+        return x;
+    }, v);
+    if (!ok) return;
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i)
+        if (mr_out_ok<F>(t, i)) zf[b * zbs + (int64_t)mr_out_pos<F>(t, i) * K0 + col] = v[i];
+}
+
+template <typename T, class F>
+__global__ void __launch_bounds__(MrCol<T, F>::THREADS) prod_ifft_mr(const cplx<T>* __restrict__ zf,
+                                                                     const cplx<T>* __restrict__ zg,
+                                                                     cplx<T>* __restrict__ y, SepGeom g, int64_t J,
+                                                                     const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using CF = MrCol<T, F>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.z;
+    const int64_t j = (int)blockIdx.y / (int)g.q, w = (int)blockIdx.y % (int)g.q;
+    const int64_t k = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = k < g.M;
+    int64_t colG = k - g.a * w;
+    const bool wrap = colG < 0;
+    if (wrap) colG += g.K0;
+    const C* zfb = zf + b * g.L + k;
+    const C* zgj = zg + j * g.L + colG;
+    C v[F::V];
+    fft_mr<F, +1, CF::W>(c, t, sm, tw, [&](int xi) -> C {
+        if (!ok) return mk((T)0, (T)0);
+        C x = cmulc(zfb[(int64_t)xi * g.K0], zgj[(int64_t)xi * g.K0]);
+        if (wrap) x = cmulc(x, __ldg(tw + xi));
+        return x;
+    }, v);
+    if (!ok) return;
+    const T scale = (T)1 / (T)F::N;
+    C* yb = y + ((b * J + j) * g.d * g.q + w) * g.M + k;
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i)
+        if (mr_out_ok<F>(t, i)) yb[(int64_t)g.q * mr_out_pos<F>(t, i) * g.M] = cscale(v[i], scale);
+}
+
+template <typename T, class F>
+__global__ void __launch_bounds__(MrCol<T, F>::THREADS, MrCol<T, F>::MINB_ADJ) fft_prod_adj_mr(const cplx<T>* __restrict__ y,
+                                                                        const cplx<T>* __restrict__ zg,
+                                                                        cplx<T>* __restrict__ zf, SepGeom g, int64_t J,
+                                                                        const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    using CF = MrCol<T, F>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = k < g.M;
+    const T scale = (T)1 / (T)F::N;
+    C acc[F::OUT];
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i) acc[i] = mk((T)0, (T)0);
+    for (int64_t j = 0; j < J; ++j) {
+        for (int64_t w = 0; w < g.q; ++w) {
+            const C* yb = y + ((b * J + j) * g.d * g.q + w) * g.M + k;
+            C v[F::V];
+            fft_mr<F, -1, CF::W>(c, t, sm, tw, [&](int nu) -> C {
+                return ok ? yb[(int64_t)g.q * nu * g.M] : mk((T)0, (T)0);
+            }, v);
+            int64_t colG = k - g.a * w;
+            const bool wrap = colG < 0;
+            if (wrap) colG += g.K0;
+            const C* zgj = zg + j * g.L + colG;
+            if (ok) {
+#pragma unroll
+                for (int i = 0; i < F::OUT; ++i) {
+                    if (!mr_out_ok<F>(t, i)) continue;
+                    const int xi = mr_out_pos<F>(t, i);
+                    C u = cmul(cscale(v[i], scale), zgj[(int64_t)xi * g.K0]);
+                    if (wrap) u = cmul(u, __ldg(tw + xi));
+                    acc[i] = cadd(acc[i], u);
+                }
+            }
+            __syncthreads();          // the next transform reuses the exchange buffer
+        }
+    }
+    if (!ok) return;
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i)
+        if (mr_out_ok<F>(t, i)) zf[b * g.L + (int64_t)mr_out_pos<F>(t, i) * g.K0 + k] = acc[i];
+}
+
+template <typename T, class F>
+__global__ void __launch_bounds__(MrCol<T, F>::THREADS) zak_inv_mr(const cplx<T>* __restrict__ zf, int64_t zbs,
+                                                                   void* __restrict__ dst, int dst_real, int64_t dbs,
+                                                                   int64_t K0, const cplx<T>* __restrict__ tw,
+                                                                   ChirpParams<cplx<T>> post, T scale) {
+    using C = cplx<T>;
+    using CF = MrCol<T, F>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.y;
+    const int64_t col = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = col < K0;
+    C v[F::V];
+    fft_mr<F, +1, CF::W>(c, t, sm, tw, [&](int xi) -> C {
+        return ok ? zf[b * zbs + (int64_t)xi * K0 + col] : mk((T)0, (T)0);
+    }, v);
+    if (!ok) return;
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i) {
+        if (!mr_out_ok<F>(t, i)) continue;
+        const int64_t l = col + K0 * mr_out_pos<F>(t, i);
+        C x = cscale(v[i], scale);
+        if (post.mode == PRE_CHIRP) x = cmul(x, chirp_factor(post, l));
+        store_any(dst, dst_real, b * dbs + l, x);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// the lengths with a compiled mixed-radix transform: N, threads per transform, radices
+// ------------------------------------------------------------------------------------
+using Mr60 = Mixed<60, 4, RadixList<4, 15>>;
+using Mr120 = Mixed<120, 8, RadixList<8, 15>>;
+using Mr180 = Mixed<180, 12, RadixList<4, 5, 9>>;
+using Mr240 = Mixed<240, 16, RadixList<16, 15>>;
+using Mr360 = Mixed<360, 24, RadixList<8, 9, 5>>;
+using Mr480 = Mixed<480, 32, RadixList<16, 2, 15>>;
+using Mr720 = Mixed<720, 48, RadixList<16, 9, 5>>;
+using Mr960 = Mixed<960, 64, RadixList<16, 4, 15>>;
+using Mr2160 = Mixed<2160, 144, RadixList<16, 9, 15>>;
+
+#define MR_SWITCH(NV, ...)                                \
+    switch (NV) {                                          \
+        case 60: { using FF = Mr60; __VA_ARGS__; }                \
+        case 120: { using FF = Mr120; __VA_ARGS__; }              \
+        case 180: { using FF = Mr180; __VA_ARGS__; }              \
+        case 240: { using FF = Mr240; __VA_ARGS__; }              \
+        case 360: { using FF = Mr360; __VA_ARGS__; }              \
+        case 480: { using FF = Mr480; __VA_ARGS__; }              \
+        case 720: { using FF = Mr720; __VA_ARGS__; }              \
+        case 960: { using FF = Mr960; __VA_ARGS__; }              \
+        case 2160: { using FF = Mr2160; __VA_ARGS__; }            \
+        default: return cudaErrorNotSupported;             \
+    }
+
+template <typename T, class F, bool POST>
+cudaError_t mr_rows_n(const cplx<T>* src, cplx<T>* dst, const SepGeom& g, int64_t J, const void* tw,
+                      const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    if (pp.half) return cudaErrorNotSupported;
+    using RC = MrRow<F>;
+    const size_t smem = sizeof(cplx<T>) * (size_t)F::SMEM * RC::RPB;
+    const bool sh1 = pp.mode == POST_SHEAR1;
+    auto k = POST ? (sh1 ? fft_post_mr<T, F, true> : fft_post_mr<T, F, false>)
+                  : (sh1 ? pre_ifft_mr<T, F, true> : pre_ifft_mr<T, F, false>);
+    cudaError_t e = p2_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t rows = B * J * g.d * g.q;
+    PostParams<cplx<T>> q = pp;
+    q.mJN = make_mod((uint64_t)(J * g.d * g.q));
+    q.mNs = make_mod((uint64_t)(g.d * g.q));
+    k<<<(unsigned)((rows + RC::RPB - 1) / RC::RPB), RC::THREADS, smem, st>>>(src, dst, g, J, rows,
+                                                                            (const cplx<T>*)tw, q);
+    return cudaGetLastError();
+}
+
+// run-time dispatch; cudaErrorNotSupported = a length without a compiled transform
+template <typename T>
+cudaError_t mr_fft_post(const cplx<T>* y, cplx<T>* c, const SepGeom& g, int64_t J, const void* tw,
+                        const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    MR_SWITCH(g.M, return (mr_rows_n<T, FF, true>(y, c, g, J, tw, pp, B, st)))
+}
+template <typename T>
+cudaError_t mr_pre_ifft(const cplx<T>* c, cplx<T>* y, const SepGeom& g, int64_t J, const void* tw,
+                        const PostParams<cplx<T>>& pp, int64_t B, cudaStream_t st) {
+    MR_SWITCH(g.M, return (mr_rows_n<T, FF, false>(c, y, g, J, tw, pp, B, st)))
+}
+
+// column launchers; cudaErrorNotSupported = a length without a compiled transform (or p != 1)
+template <typename T, class F, class K> cudaError_t mr_col_prep(K k) { return p2_smem(k, MrCol<T, F>::SMEM); }
+
+template <typename T>
+cudaError_t mr_zak_fwd(const void* src, int src_real, int64_t sbs, cplx<T>* zf, int64_t zbs, int64_t d, int64_t K0,
+                       const void* tw, const ChirpParams<cplx<T>>& pre, int64_t B, cudaStream_t st) {
+    MR_SWITCH(d, {
+        using CF = MrCol<T, FF>;
+        auto k = zak_fwd_mr<T, FF>;
+        cudaError_t e = mr_col_prep<T, FF>(k);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((K0 + CF::W - 1) / CF::W), (unsigned)B);
+        k<<<grid, CF::THREADS, CF::SMEM, st>>>(src, src_real, sbs, zf, zbs, K0, (const cplx<T>*)tw, pre);
+        return cudaGetLastError();
+    })
+}
+template <typename T>
+cudaError_t mr_prod_ifft(const cplx<T>* zf, const cplx<T>* zg, int64_t J, cplx<T>* y, const SepGeom& g,
+                         const void* tw, int64_t B, cudaStream_t st) {
+    if (g.p != 1) return cudaErrorNotSupported;
+    MR_SWITCH(g.d, {
+        using CF = MrCol<T, FF>;
+        auto k = prod_ifft_mr<T, FF>;
+        cudaError_t e = mr_col_prep<T, FF>(k);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((g.M + CF::W - 1) / CF::W), (unsigned)(J * g.q), (unsigned)B);
+        k<<<grid, CF::THREADS, CF::SMEM, st>>>(zf, zg, y, g, J, (const cplx<T>*)tw);
+        return cudaGetLastError();
+    })
+}
+template <typename T>
+cudaError_t mr_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx<T>* zf, const SepGeom& g,
+                            const void* tw, int64_t B, cudaStream_t st) {
+    if (g.p != 1) return cudaErrorNotSupported;
+    MR_SWITCH(g.d, {
+        using CF = MrCol<T, FF>;
+        auto k = fft_prod_adj_mr<T, FF>;
+        cudaError_t e = mr_col_prep<T, FF>(k);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((g.M + CF::W - 1) / CF::W), (unsigned)B);
+        k<<<grid, CF::THREADS, CF::SMEM, st>>>(y, zg, zf, g, J, (const cplx<T>*)tw);
+        return cudaGetLastError();
+    })
+}
+template <typename T>
+cudaError_t mr_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
+                       const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st) {
+    MR_SWITCH(d, {
+        using CF = MrCol<T, FF>;
+        auto k = zak_inv_mr<T, FF>;
+        cudaError_t e = mr_col_prep<T, FF>(k);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((K0 + CF::W - 1) / CF::W), (unsigned)B);
+        k<<<grid, CF::THREADS, CF::SMEM, st>>>(zf, zbs, dst, dst_real, dbs, K0, (const cplx<T>*)tw, post, scale);
+        return cudaGetLastError();
+    })
+}
+
+}  // namespace dgt

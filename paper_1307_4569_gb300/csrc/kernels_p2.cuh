@@ -483,6 +483,16 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) fft_post_p2(const cplx<T>*
         C v[16];
         fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? yr[k] : mk((T)0, (T)0); }, v);
         if (!ok) return;
+        if (pp.sh1_fast) {
+            const Sh1Row sr = sh1_row(pp, b, nn);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                C ph;
+                const int64_t o = sh1_at(pp, sr, p2_out_pos<N>(t, i), ph);
+                c[o] = cmul(v[i], ph);
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             C ph;
@@ -530,12 +540,22 @@ __global__ void __launch_bounds__(RowCfg<N>::THREADS) pre_ifft_p2(const cplx<T>*
     const int64_t j = ok ? (int64_t)pp.mNs.div((uint64_t)rem) : 0, nn = ok ? rem - j * (int64_t)pp.mNs.d : 0;
     C v[16];
     if constexpr (SH1) {
-        fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
-            if (!ok) return mk((T)0, (T)0);
-            C ph;
-            const int64_t o = out_index(pp, g, b, j, nn, m, ph);
-            return cmulc(c[o], ph);
-        }, v);
+        if (pp.sh1_fast) {
+            const Sh1Row sr = sh1_row(pp, b, nn);
+            fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                if (!ok) return mk((T)0, (T)0);
+                C ph;
+                const int64_t o = sh1_at(pp, sr, m, ph);
+                return cmulc(c[o], ph);
+            }, v);
+        } else {
+            fft_p2<N, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+                if (!ok) return mk((T)0, (T)0);
+                C ph;
+                const int64_t o = out_index(pp, g, b, j, nn, m, ph);
+                return cmulc(c[o], ph);
+            }, v);
+        }
     } else {
         RowMap<C> rm{};
         if (ok) rm = row_map(pp, g, b, j, nn);

@@ -539,6 +539,17 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             pp.C5_2N = k.C5m;
             pp.s1ar_L = pmod(-(int64_t)(((__int128)k.sh.s1 * k.ar) % k.L), k.L);
             pp.C6_L = pmod(k.C6, k.L);
+            // 32-bit per-row form when every product stays below 2^32
+            if (twoN < 65536 && (uint64_t)k.L * (uint64_t)(k.Nr + 1) < ((uint64_t)1 << 32)) {
+                pp.sh1_fast = 1;
+                pp.f_Nr = (uint32_t)k.Nr; pp.f_N = (uint32_t)k.N; pp.f_M = (uint32_t)k.M;
+                pp.f_C1 = (uint32_t)pp.C1_2N_; pp.f_C2 = (uint32_t)pp.C2_2N; pp.f_C3 = (uint32_t)pp.C3_2N;
+                pp.f_C4 = (uint32_t)pp.C4_2N; pp.f_C5 = (uint32_t)pp.C5_2N;
+                pp.f_s1ar = (uint32_t)pp.s1ar_L; pp.f_C6 = (uint32_t)pp.C6_L;
+                pp.q2N = make_mod32((uint32_t)twoN);
+                pp.qL = make_mod32((uint32_t)k.L);
+                pp.qb = make_mod32((uint32_t)k.b);
+            }
         }
         return pp;
     }
@@ -905,17 +916,19 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         pp.mN = make_mod((uint64_t)k.N);
         pp.m2N = make_mod(2 * (uint64_t)k.N);
         pp.mb = make_mod((uint64_t)k.b);
+        const int64_t groups = fft_grad_window_groups(cg, k.lam2, B, sizeof(C));
         const size_t need = al(sizeof(C) * (size_t)B * k.L) + al(sizeof(C) * (size_t)B * k.M * k.N) +
-                            2 * al(sizeof(C) * (size_t)k.lam2 * k.L);
+                            2 * al(sizeof(C) * (size_t)k.lam2 * k.L) + al(sizeof(C) * (size_t)groups * k.lam2 * k.L);
         DGT_TRY(gradws.alloc(need));               // plan-owned, grown on demand
         char* p = (char*)gradws.p;
         C* zf = (C*)p; p += al(sizeof(C) * (size_t)B * k.L);
         C* y = (C*)p; p += al(sizeof(C) * (size_t)B * k.M * k.N);
         C* v = (C*)p; p += al(sizeof(C) * (size_t)k.lam2 * k.L);
-        C* wj = (C*)p;
+        C* wj = (C*)p; p += al(sizeof(C) * (size_t)k.lam2 * k.L);
+        C* part = (C*)p;
         KTRY("zak_fwd", st, launch_zak_fwd<T>(f, f_real, k.L, zf, k.L, k.L, cg.d, *fd, nochirp(), B, st));
         KTRY("pre_ifft", st, launch_pre_ifft<T>((const C*)G, y, cg, k.lam2, *fft(cg.M), pp, B, st));
-        KTRY("fft_grad_window", st, launch_fft_grad_window<T>(y, zf, k.lam2, v, cg, *fd, B, st));
+        KTRY("fft_grad_window", st, launch_fft_grad_window<T>(y, zf, k.lam2, v, part, cg, *fd, B, st));
         KTRY("zak_inv", st, launch_zak_inv<T>(v, k.L, wj, 0, k.L, k.L, cg.d, *fd, nochirp(), (T)1, k.lam2, st));
         KTRY("grad_window_combine", st, launch_grad_window_combine<T>(wj, grad, grad_real, k.L, k.a, k.lam2, (const int64_t*)sigma.p,
                                                cisL.tab, st));
