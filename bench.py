@@ -472,6 +472,9 @@ def run_ours(args, rank, world):
     if args.serve_seconds > 0 and rank == 0:      # replicas: the serving run is a one-GPU measurement
         serve = run_serve(args.serve_seconds)
     others = run_other_configs(dev) if (args.other_configs and rank == 0) else None
+    if others is not None:
+        # the experiment of Fig. 2: coset and shear analysis times as lambda2 goes from 1 to 10
+        others["lambda_sweep"] = run_lambda_sweep(dev, steps=3)
 
     # ---------------- CPU baseline (oracle), rank 0 only ----------------
     cpu = None

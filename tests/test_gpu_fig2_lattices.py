@@ -1,0 +1,64 @@
+"""The lattices of the paper's timing experiment (Section 4.4, Fig. 2): (a, M) in {(32, 64),
+(40, 60), (60, 80)}, L = lcm(a, M) 2520, lambda1 = 1, lambda2 in {2, 6, 9}, periodised
+Gaussian window, float32; both routes against the oracle's fold form on sampled time
+positions (first, last, one per coset class), and the coset and shear results against each
+other.  A lattice whose shear route needs a transform longer than this build's tile is refused
+with DGT_ERR_UNSUPPORTED at plan creation (the coset route still runs it)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dgt as OD  # noqa: E402
+from workloads import complex_normal, gaussian_window  # noqa: E402
+
+TOL = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1307_4569_gb300 import build
+
+    build.build()
+
+
+@pytest.mark.parametrize("lam2", [2, 6, 9])
+@pytest.mark.parametrize("aM", [(32, 64), (40, 60), (60, 80)])
+def test_fig2_lattice(aM, lam2):
+    from paper_1307_4569_gb300 import DGTError, Plan
+
+    a, M = aM
+    L = a * M // math.gcd(a, M) * 2520
+    N = L // a
+    g = gaussian_window(L).astype(np.float32).astype(np.float64)
+    B = 2
+    f = np.stack([complex_normal(L, 97, lam2, i) for i in range(B)]).astype(np.complex64)
+    fd = torch.from_numpy(f).cuda()
+    f64 = f.astype(np.complex128)
+    cols = sorted({0, 1, lam2 - 1, lam2, N // 2 + 1, N - 1})
+    outs = {}
+    for route in ("coset", "shear"):
+        try:
+            p = Plan(L, a, M, 1, lam2, g, route=route, precision="f32")
+        except DGTError as e:
+            assert route == "shear" and "DGT_ERR_UNSUPPORTED" in str(e), e
+            continue
+        c = p.dgt(fd)
+        for b in range(B):
+            ref = OD.dgt_fold(f64[b], g, a, M, 1, lam2, cols=cols)
+            got = c[b, cols, :].cpu().numpy().T.astype(np.complex128)
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err <= TOL, (route, aM, lam2, b, err, p.info)
+        outs[route] = c
+        p.status()
+        p.close()
+    if len(outs) == 2:
+        for b in range(B):
+            d = float(torch.linalg.vector_norm(outs["coset"][b] - outs["shear"][b]) /
+                      torch.linalg.vector_norm(outs["coset"][b]))
+            assert d <= 2 * TOL, (aM, lam2, b, d)
