@@ -351,6 +351,8 @@ def run_ours(args, rank, world):
         os.sched_setaffinity(0, old_aff)
     host_nodes = page_nodes(c_hosts + fr_hosts + [f_host])
     d2h_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nroutes)]
+    fr_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nroutes)]
+    h2d_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     cbufs = [cbuf] + [torch.empty_like(cbuf) for _ in range(nroutes - 1)]
     frs = [fr] + [torch.empty_like(fr) for _ in range(nroutes - 1)]
     cs = torch.cuda.Stream(dev)
@@ -359,7 +361,9 @@ def run_ours(args, rank, world):
 
     def e2e_step():
         cur = torch.cuda.current_stream(dev)
+        h2d_ev[0].record(cur)
         fin.copy_(f_host, non_blocking=True)
+        h2d_ev[1].record(cur)
         for r, (_, p) in enumerate(plans):
             if copied[r] is not None:
                 cur.wait_event(copied[r])        # the previous step's copies of this route's buffers
@@ -375,7 +379,9 @@ def run_ours(args, rank, world):
                 c_hosts[r].copy_(cbufs[r], non_blocking=True)
                 d2h_ev[r][1].record(cs)
                 cs.wait_event(e_f)
+                fr_ev[r][0].record(cs)
                 fr_hosts[r].copy_(frs[r], non_blocking=True)
+                fr_ev[r][1].record(cs)
                 copied[r] = torch.cuda.Event()
                 copied[r].record(cs)
         cur.wait_stream(cs)                      # the step ends when its results are on the host
@@ -386,13 +392,20 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps - 1)]
     a0.record()
-    for _ in range(e2e_steps):
+    for i in range(e2e_steps):
         e2e_step()
+        if i < e2e_steps - 1:
+            marks[i].record()
     a1.record()
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(a0.elapsed_time(a1) / e2e_steps, world, dev)
+    bounds = [a0] + marks + [a1]
+    e2e_per_step = [bounds[i].elapsed_time(bounds[i + 1]) for i in range(e2e_steps)]
     d2h_ms = [e0.elapsed_time(e1) for e0, e1 in d2h_ev]          # last step, per route
+    fr_ms = [e0.elapsed_time(e1) for e0, e1 in fr_ev]
+    h2d_ms = h2d_ev[0].elapsed_time(h2d_ev[1])
     te = time.time()
     clocks.stop()
     clk = clocks.summary(t0, te)
@@ -498,6 +511,13 @@ def run_ours(args, rank, world):
                 "steps": e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "coef_copy_ms_per_route": d2h_ms,
                 "coef_copy_gbs_per_route": [B * w.N * w.M * 8 / (x * 1e-3) / 1e9 if x > 0 else None for x in d2h_ms],
+                "signal_copy_ms_per_route": fr_ms, "input_copy_ms": h2d_ms,
+                "per_step_ms": e2e_per_step, "median_ms_per_step": statistics.median(e2e_per_step),
+                "link_floor_ms": d2h / (max(B * w.N * w.M * 8 / (x * 1e-3) for x in d2h_ms if x > 0)) * 1e3
+                if any(x > 0 for x in d2h_ms) else None,
+                "note": "the device-to-host bytes of a step cross the host link, measured at about 193 GB/s by the "
+                        "copy engine and by SM stores alike; occasional copies 3-8 times slower than that, at "
+                        "changing points of a run of identical steps, raise the mean above the median",
                 "gpu_numa_node": node, "gpu_local_cpus": len(cpus) if cpus else None,
                 "pinned_buffer_numa_nodes": host_nodes},
         "fp64": fp64,
@@ -894,7 +914,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-procs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0, help="signals per step (default: the workload's 64)")
