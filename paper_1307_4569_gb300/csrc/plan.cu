@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -141,7 +142,11 @@ struct ShearSel {
 // then s1 = -(s + k b)/a and the separable lattice is (a, b).  Otherwise the smallest s1 >= 0
 // is taken for which eq. (modcond)  s0 X + a k1 = 0 (mod a b / X)  is solvable, with
 // X = gcd(s1 a + s, b) = k1 (s1 a + s) + k2 b; the separable lattice is diag(a b / X, X).
-static bool shear_select(int64_t L, int64_t a, int64_t b, int64_t s, ShearSel& out) {
+// Every valid pair gives the same coefficients; among the frequency shears the first one in
+// that order whose separable lattice this build can transform is taken (`runs`, given b_r = X),
+// so that a lattice is refused only when none of them fits.
+static bool shear_select(int64_t L, int64_t a, int64_t b, int64_t s, ShearSel& out,
+                         const std::function<bool(int64_t)>& runs) {
     if (s == 0) {
         out = {0, 0, b};
         return true;
@@ -152,17 +157,24 @@ static bool shear_select(int64_t L, int64_t a, int64_t b, int64_t s, ShearSel& o
         out = {0, pmod(-(num / a), L), b};
         return true;
     }
+    bool found = false;
     for (int64_t s1 = 0; s1 < L; ++s1) {
         int64_t k1, k2;
         const int64_t X = egcd(s1 * a + s, b, k1, k2);
         const int64_t mod = a * b / X;
         const int64_t s0 = solve_congruence(X, -a * k1, mod);
         if (s0 >= 0) {
-            out = {pmod(s0, L), s1, X};
-            return true;
+            if (!found) {
+                out = {pmod(s0, L), s1, X};
+                found = true;
+            }
+            if (runs(X)) {
+                out = {pmod(s0, L), s1, X};
+                return true;
+            }
         }
     }
-    return false;
+    return found;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1046,7 +1058,13 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
     k.coset_sep = make_sep(L, lam2 * a, M);
 
     // shear parameters (always computed; reported by dgt_plan_get_info)
-    if (!shear_select(L, a, k.b, k.s, k.sh)) return fail(DGT_ERR_ARG, "no shear found");
+    // a frequency shear with b_r = X runs the separable lattice (X, L / (a b / X)) of FFT(f)
+    auto freq_sep_runs = [&](int64_t X) {
+        const int64_t ar = a * k.b / X;
+        const SepGeom sg = make_sep(L, X, L / ar);
+        return fft_ok(sg.d, precision) && fft_rows_ok(sg.M, precision);
+    };
+    if (!shear_select(L, a, k.b, k.s, k.sh, freq_sep_runs)) return fail(DGT_ERR_ARG, "no shear found");
     k.freq_shear = k.sh.s0 != 0;
 
     // FIR chunking: columns per CTA, a divisor of N, fitting the shared-memory tile;

@@ -2,8 +2,9 @@
 (40, 60), (60, 80)}, L = lcm(a, M) 2520, lambda1 = 1, lambda2 in {2, 6, 9}, periodised
 Gaussian window, float32; both routes against the oracle's fold form on sampled time
 positions (first, last, one per coset class), and the coset and shear results against each
-other.  A lattice whose shear route needs a transform longer than this build's tile is refused
-with DGT_ERR_UNSUPPORTED at plan creation (the coset route still runs it)."""
+other.  (32, 64) at lambda2 = 6 needs a frequency shear; its first shear pair would put a Zak
+length of 20160 on the device, beyond the shared-memory tile, so the planner takes the next pair
+whose separable lattice it can transform (any valid pair gives the same coefficients)."""
 import math
 
 import numpy as np
@@ -30,7 +31,7 @@ def _built():
 @pytest.mark.parametrize("lam2", [2, 6, 9])
 @pytest.mark.parametrize("aM", [(32, 64), (40, 60), (60, 80)])
 def test_fig2_lattice(aM, lam2):
-    from paper_1307_4569_gb300 import DGTError, Plan
+    from paper_1307_4569_gb300 import Plan
 
     a, M = aM
     L = a * M // math.gcd(a, M) * 2520
@@ -43,11 +44,7 @@ def test_fig2_lattice(aM, lam2):
     cols = sorted({0, 1, lam2 - 1, lam2, N // 2 + 1, N - 1})
     outs = {}
     for route in ("coset", "shear"):
-        try:
-            p = Plan(L, a, M, 1, lam2, g, route=route, precision="f32")
-        except DGTError as e:
-            assert route == "shear" and "DGT_ERR_UNSUPPORTED" in str(e), e
-            continue
+        p = Plan(L, a, M, 1, lam2, g, route=route, precision="f32")
         c = p.dgt(fd)
         for b in range(B):
             ref = OD.dgt_fold(f64[b], g, a, M, 1, lam2, cols=cols)
@@ -57,6 +54,7 @@ def test_fig2_lattice(aM, lam2):
         outs[route] = c
         p.status()
         p.close()
+    assert len(outs) == 2
     if len(outs) == 2:
         for b in range(B):
             d = float(torch.linalg.vector_norm(outs["coset"][b] - outs["shear"][b]) /
