@@ -99,3 +99,37 @@ def test_serve_mixed_equals_alone_and_oracle():
             checked_oracle += 1
     assert checked_oracle >= 2
     ex.close()
+
+
+def test_expired_wait_marks_only_its_batch():
+    """A synthesis batch whose tile-copy waits expire (the wait limit set to zero through the
+    test hook; no fault involved) is reported by its own workspace word when the executor
+    finishes it: finish() raises DGT_ERR_TIMEOUT for that batch, and the next batch of the same
+    plan on the same stream arena finishes cleanly with the correct result."""
+    from paper_1307_4569_gb300 import DGTError
+    from paper_1307_4569_gb300 import _capi as K
+    from paper_1307_4569_gb300.serve import GpuExecutor
+
+    # d = L / M = 1024 for a = 64, M = 256: the float synthesis stages its tiles with the TMA
+    key = (1 << 18, 64, 256, 1, 2, "gauss")
+    ex = GpuExecutor("f32", streams=2, arena_bytes=1 << 30, keep_results=True)
+    ex.prepare(key)
+    assert ex.plans[key].info["d"] == 1024
+    old = K.lib().dgt_wait_limit(0)
+    try:
+        h = ex.launch(key, "idgt", [None] * 2, [0, 1])
+        with pytest.raises(DGTError, match="DGT_ERR_TIMEOUT"):
+            ex.finish(h)
+    finally:
+        K.lib().dgt_wait_limit(old)
+    h = ex.launch(key, "idgt", [None] * 2, [2, 3])
+    ex.finish(h)
+    # the clean batch against the oracle's synthesis of the same inputs
+    L, a, M, l1, l2, _ = key
+    gd = OU.zak_gram_dual(gaussian_window(L), a, M, l1, l2)       # the plan's dual comes from the float64 window
+    for rid in (2, 3):
+        cin = ex._input(key, "idgt", rid).numpy().astype(np.complex128)
+        want = OD.idgt_fold(cin.T, gd, a, M, l1, l2)
+        got = ex.results[rid].numpy().astype(np.complex128)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 2e-6
+    ex.close()
