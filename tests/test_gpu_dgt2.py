@@ -58,10 +58,11 @@ def test_dgt2(case, route, prec):
     for b in range(B):
         ref = O2.dgt2(fr[b], _r(g1, prec).real, _r(g2, prec).real, lat1[1:], lat2[1:])   # [m1, n1, m2, n2]
         assert _rel(cn[b].transpose(1, 0, 3, 2), ref) <= TOL[prec], (b, _rel(cn[b].transpose(1, 0, 3, 2), ref))
-    # adjoint against the oracle
-    u = cn[0].transpose(1, 0, 3, 2).astype(np.complex128)
-    fa = p.idgt(c[:1].contiguous(), window="adjoint").cpu().numpy()[0]
-    assert _rel(fa, O2.idgt2(_r(u, prec), _r(g1, prec).real, _r(g2, prec).real, lat1[1:], lat2[1:])) <= TOL[prec]
+    # adjoint of the oracle's own coefficients against the oracle's adjoint
+    u = _r(O2.dgt2(fr[0], _r(g1, prec).real, _r(g2, prec).real, lat1[1:], lat2[1:]), prec)   # [m1, n1, m2, n2]
+    ud = torch.from_numpy(np.ascontiguousarray(u.transpose(1, 0, 3, 2))[None]).to(dt).cuda()
+    fa = p.idgt(ud, window="adjoint").cpu().numpy()[0]
+    assert _rel(fa, O2.idgt2(u, _r(g1, prec).real, _r(g2, prec).real, lat1[1:], lat2[1:])) <= TOL[prec]
     # reconstruction with the tensor product of the duals
     rec = p.idgt(c, window="dual").cpu().numpy()
     for b in range(B):

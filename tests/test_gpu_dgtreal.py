@@ -62,9 +62,14 @@ def test_dgtreal(lat, route, prec):
     assert rec.dtype == dt
     for b in range(B):
         assert _rel(rec[b].cpu().numpy(), fr[b]) <= 5 * TOL[prec]
-    # the adjoint from the half channels equals the oracle's real synthesis with g
-    fa = p.idgtreal(ch, window="adjoint").cpu().numpy()
-    assert _rel(fa[0], OR.idgtreal(chn[0].T, _r(g, prec), a, M, l1, l2)) <= TOL[prec]
+    # the adjoint from the oracle's half channels equals the oracle's real synthesis with g
+    hc = OR.dgtreal(fr[0], _r(g, prec), a, M, l1, l2)                     # [m <= M/2, n]
+    if prec == "f32":
+        hc = hc.astype(np.complex64).astype(np.complex128)
+    cd = torch.complex128 if prec == "f64" else torch.complex64
+    hd = torch.from_numpy(np.ascontiguousarray(hc.T)[None]).to(cd).cuda()
+    fa = p.idgtreal(hd, window="adjoint").cpu().numpy()
+    assert _rel(fa[0], OR.idgtreal(hc, _r(g, prec), a, M, l1, l2)) <= TOL[prec]
     p.close()
 
 

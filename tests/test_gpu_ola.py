@@ -81,10 +81,10 @@ def test_ola_plan(case, route, prec):
     for b in range(B):
         ref = OD.dgt_coset(fr[b], gfull, a, M, l1, l2).T
         assert _rel(c[b], ref) <= TOL[prec], (b, _rel(c[b], ref))
-    # the adjoint against the oracle's blockwise synthesis (same Lx)
-    u = c[0].T.astype(np.complex128)
-    fa = p.idgt(_dev(c[0], prec), window="adjoint").cpu().numpy()
-    assert _rel(fa, OO.idgt_ola(_r(u, prec), tr, center, a, M, l1, l2, Lb, Lx)) <= TOL[prec]
+    # the adjoint of the oracle's coefficients against the oracle's blockwise synthesis (same Lx)
+    u = _r(OD.dgt_coset(fr[0], gfull, a, M, l1, l2), prec)               # [m, n]
+    fa = p.idgt(_dev(np.ascontiguousarray(u.T), prec), window="adjoint").cpu().numpy()
+    assert _rel(fa, OO.idgt_ola(u, tr, center, a, M, l1, l2, Lb, Lx)) <= TOL[prec]
     # reconstruction with the dual (windows no longer than M), and the dual itself
     if Lg <= M:
         gd = OU.fir_dual_diag(gfull, a, M)

@@ -194,9 +194,9 @@ def test_fir_route(params, prec):
     fr = p.idgt(_to_dev(c, prec), window="dual", real=True).cpu().numpy()
     for b in range(B):
         assert _rel(fr[b], _round(f[b], prec)) <= 5 * TOL[prec]
-    cc = c[0]
-    fa = p.idgt(_to_dev(cc, prec), window="adjoint").cpu().numpy()
-    assert _rel(fa, OD.idgt_fold(cc.T.astype(np.complex128), _round(gfull, prec), a, M, l1, l2)) <= TOL[prec]
+    cc = _round(OD.dgt_fold(_round(f[0], prec), _round(gfull, prec), a, M, l1, l2), prec)   # the oracle's [m, n]
+    fa = p.idgt(_to_dev(np.ascontiguousarray(cc.T), prec), window="adjoint").cpu().numpy()
+    assert _rel(fa, OD.idgt_fold(cc, _round(gfull, prec), a, M, l1, l2)) <= TOL[prec]
 
 
 # -------------------------------------------------------------------------------------
