@@ -947,9 +947,9 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_pair_p2
     const int S = a * (nc - 1) + Lg;
     const int D = (Lg + a - 1) / a;
     const int PR = nc / D;                           // columns per round
-    T* h = acc + S;                                  // the real taps
+    // the real taps: row wn = 0 of the modulated taps (real parts), read through L1
+    const T* h = reinterpret_cast<const T*>(fp.mtaps);
     for (int i = threadIdx.x; i < S; i += RC::THREADS) acc[i] = (T)0;
-    for (int i = threadIdx.x; i < Lg; i += RC::THREADS) h[i] = fp.mtaps[i].x;
     __syncthreads();
     for (int dq = 0; dq < D / 2; ++dq) {
         const int q1 = (dq / lam2) * 2 * lam2 + dq % lam2;
@@ -1018,7 +1018,7 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_pair_p2
                 for (int i = 0; i < 16; ++i) {
                     const int k = p2_out_pos<N>(t, i);
                     const int tap = (k - lnm1) & (N - 1);
-                    if (tap < Lg) ar[tap] += ((dh && k < lnm1) ? -sg1 : sg1) * h[tap] * v[i].x;
+                    if (tap < Lg) ar[tap] += ((dh && k < lnm1) ? -sg1 : sg1) * __ldg(h + 2 * tap) * v[i].x;
                 }
             }
             __syncthreads();                        // columns of the rounds q and q + lambda2 overlap
@@ -1028,7 +1028,7 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_pair_p2
                 for (int i = 0; i < 16; ++i) {
                     const int k = p2_out_pos<N>(t, i);
                     const int tap = (k - lnm2) & (N - 1);
-                    if (tap < Lg) ar[tap] += ((dh && k < lnm2) ? -sg2 : sg2) * h[tap] * v[i].y;
+                    if (tap < Lg) ar[tap] += ((dh && k < lnm2) ? -sg2 : sg2) * __ldg(h + 2 * tap) * v[i].y;
                 }
             }
             __syncthreads();
@@ -1316,7 +1316,7 @@ template <typename T, int N, int DIV>
 cudaError_t p2_fir_synthesis_pair_launch(const cplx<T>* c, void* f, cplx<T>* seams, const FirParams<cplx<T>>& fp,
                                          const void* tw, int64_t B, cudaStream_t st) {
     const size_t smem = sizeof(cplx<T>) * (size_t)Pow2<N>::SMEM * SynCfg<N, DIV>::RPB +
-                        sizeof(T) * (size_t)(fp.a * (fp.cols - 1) + 2 * fp.Lg);
+                        sizeof(T) * (size_t)(fp.a * (fp.cols - 1) + fp.Lg);
     if (smem > kSmemBudget) return cudaErrorNotSupported;
     auto k = fir_synthesis_pair_p2<T, N, DIV>;
     cudaError_t e = p2_smem(k, smem);
