@@ -68,6 +68,7 @@ template <typename C> struct ChirpParams {
     int conj;                         // multiply by the conjugate chirp
     CisTable<C> cis2L;                // exp(2 pi i e / (2L))
     ModU64 m2L;                       // reduction modulo 2L
+    const C* tab;                     // the unconjugated chirp at l < L when the plan built it, else null
 };
 
 // ------------------------------------------------------------------------------------
@@ -176,6 +177,8 @@ cudaError_t launch_transpose(const cplx<T>* in, cplx<T>* out, int64_t R, int64_t
 template <typename T>
 cudaError_t launch_coset_windows(const cplx<T>* g, cplx<T>* gj, int64_t L, int64_t a, int64_t J, const int64_t* sigma,
                                  const CisTable<cplx<T>>& cisL, cudaStream_t st);
+template <typename T>
+cudaError_t launch_chirp_table(const ChirpParams<cplx<T>>& cp, cplx<T>* tab, cudaStream_t st);
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const void* in, int in_real, cplx<Tout>* out, int64_t n, cudaStream_t st);
 template <typename T>

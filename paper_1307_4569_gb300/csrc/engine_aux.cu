@@ -1,6 +1,7 @@
 // FIR (weighted overlap-add) path, window set-up, Gram blocks of the dual / tight windows,
 // the window-gradient combination and the log-magnitude loss.
 #include "engine.h"
+#include "kcommon.cuh"
 
 #include <algorithm>
 #include <map>
@@ -257,6 +258,24 @@ cudaError_t launch_coset_windows(const cplx<T>* g, cplx<T>* gj, int64_t L, int64
     const int64_t total = J * L;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
     coset_windows_kernel<T><<<blocks, 256, 0, st>>>(g, gj, L, a, J, sigma, cisL);
+    return cudaGetLastError();
+}
+
+// tab[l] = pchirp(L, s)(l), l < L (Algorithm 1's chirps), from the exact exponent: the table the
+// per-sample chirp_factor reads instead of three reductions modulo 2L and a two-level lookup
+template <typename T>
+__global__ void chirp_table_kernel(ChirpParams<cplx<T>> cp, cplx<T>* __restrict__ tab) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < cp.L; l += (int64_t)gridDim.x * blockDim.x)
+        tab[l] = chirp_exact(cp, l);
+}
+
+template <typename T>
+cudaError_t launch_chirp_table(const ChirpParams<cplx<T>>& cp, cplx<T>* tab, cudaStream_t st) {
+    ChirpParams<cplx<T>> c = cp;
+    c.conj = 0;
+    c.tab = nullptr;
+    const unsigned blocks = (unsigned)std::min<int64_t>((cp.L + 255) / 256, 152 * 32);
+    chirp_table_kernel<T><<<blocks, 256, 0, st>>>(c, tab);
     return cudaGetLastError();
 }
 
@@ -873,6 +892,7 @@ cudaError_t fma_rate(int kind, int iters, int blocks, float* out, cudaStream_t s
                                                  const FftRef&, int64_t, cudaStream_t);                               \
     template cudaError_t launch_coset_windows<T>(const cplx<T>*, cplx<T>*, int64_t, int64_t, int64_t,                 \
                                                  const int64_t*, const CisTable<cplx<T>>&, cudaStream_t);             \
+    template cudaError_t launch_chirp_table<T>(const ChirpParams<cplx<T>>&, cplx<T>*, cudaStream_t);                  \
     template cudaError_t launch_grad_window_combine<T>(const cplx<T>*, void*, int, int64_t, int64_t, int64_t,         \
                                                        const int64_t*, const CisTable<cplx<T>>&, cudaStream_t);       \
     template cudaError_t launch_logmag<T>(const cplx<T>*, cplx<T>*, double*, double*, int64_t, T, int64_t, cudaStream_t);

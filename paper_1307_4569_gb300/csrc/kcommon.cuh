@@ -5,8 +5,9 @@
 
 namespace dgt {
 
-template <typename C> __device__ __forceinline__ C chirp_factor(const ChirpParams<C>& cp, int64_t l) {
-    // pchirp(L, s)(l) = exp(pi i (s l^2 (L+1) mod 2L) / L) = exp(2 pi i e / 2L), 0 <= l < L
+// pchirp(L, s)(l) = exp(pi i (s l^2 (L+1) mod 2L) / L) = exp(2 pi i e / 2L), 0 <= l < L, from
+// the exact integer exponent (three reductions modulo 2L and a two-level table lookup)
+template <typename C> __device__ __forceinline__ C chirp_exact(const ChirpParams<C>& cp, int64_t l) {
     const uint64_t lr = (uint64_t)l;
     const uint64_t l2 = cp.m2L.mod(lr * lr);
     const uint64_t t = cp.m2L.mulmod(l2, (uint64_t)cp.L + 1);
@@ -14,6 +15,17 @@ template <typename C> __device__ __forceinline__ C chirp_factor(const ChirpParam
     C w = cp.cis2L.at(e);
     if (cp.conj) w.y = -w.y;
     return w;
+}
+
+// the chirp factor of sample l < L: one load from the plan's table of chirp_exact's values
+// (bit-identical) when it has one, else computed
+template <typename C> __device__ __forceinline__ C chirp_factor(const ChirpParams<C>& cp, int64_t l) {
+    if (cp.tab) {
+        C w = __ldg(cp.tab + l);
+        if (cp.conj) w.y = -w.y;
+        return w;
+    }
+    return chirp_exact(cp, l);
 }
 
 template <typename C> __device__ __forceinline__ C load_any(const void* p, int is_real, int64_t i) {

@@ -365,6 +365,8 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_prod_ifft_p2(const 
     const int64_t k = (int64_t)blockIdx.x * CF::W + c;
     const bool ok = k < g.M;
     const int64_t K0 = g.K0;
+    // the Zak column, scaled once by 1 / d (a power of two, so exactly as the products would be)
+    const T scale = (T)1 / (T)N;
     C zfm[16];
     {
         C v[16];
@@ -376,9 +378,8 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_prod_ifft_p2(const 
             return x;
         }, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) zfm[p2_out_m<N>(i)] = v[i];
+        for (int i = 0; i < 16; ++i) zfm[p2_out_m<N>(i)] = cscale(v[i], scale);
     }
-    const T scale = (T)1 / (T)N;
     const int64_t ystride = g.q * g.M;                     // Y rows w + q nu, nu = 0, 1, ...
     for (int64_t j = 0; j < J; ++j) {
         for (int64_t w = 0; w < g.q; ++w) {
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(ColCfg<T, N>::THREADS) zak_prod_ifft_p2(const 
             if (ok) {
                 C* yb = y + ((b * J + j) * g.d * g.q + w) * g.M + k;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) yb[(int64_t)p2_out_pos<N>(t, i) * ystride] = mk(v[i].x * scale, v[i].y * scale);
+                for (int i = 0; i < 16; ++i) yb[(int64_t)p2_out_pos<N>(t, i) * ystride] = v[i];
             }
         }
     }

@@ -435,6 +435,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     DevBuf firmt[4];                   // FIR route: modulated taps [lam2][Lg] of the windows in gam / gT
     DevBuf lossparts;
     DevBuf hbtab;                      // FIR route, lambda2 = 2: exp(-pi i k / M), k < M (real-input pairing)
+    std::map<int64_t, DevBuf> chirpt;  // shear routes: s mod 2L -> pchirp(L, s)(l), l < L
     DevBuf gradws;                     // work arrays of the window gradient
 
     const FftRef* fft(int64_t n) {
@@ -491,6 +492,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     size_t owned_bytes() const override {
         size_t s = sigma.bytes + g64.bytes + gT.bytes + work.bytes + tmpwin.bytes + status.bytes + lossparts.bytes +
                    real_full.bytes + hbtab.bytes + gradws.bytes;
+        for (auto& kv : chirpt) s += kv.second.bytes;
         for (int i = 0; i < 4; ++i) s += zg[i].bytes + gam[i].bytes + firmt[i].bytes;
         for (auto& kv : tw) s += kv.second->buf.bytes;
         s += cisL.hi.bytes + cisL.lo.bytes + cis2L.hi.bytes + cis2L.lo.bytes + cis2N.hi.bytes + cis2N.lo.bytes +
@@ -506,7 +508,25 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         cp.conj = conj;
         cp.cis2L = cis2L.tab;
         cp.m2L = make_mod(2 * (uint64_t)core.L);
+        auto it = chirpt.find(cp.s_2L);
+        cp.tab = it == chirpt.end() ? nullptr : (const C*)it->second.p;
         return cp;
+    }
+    // the chirps of Algorithm 1 (pchirp(L, s1), and pchirp(L, -s0) in the frequency-shear branch)
+    // as tables of L values, so that a kernel reads each sample's factor in one load; none
+    // beyond kChirpTableCap bytes, where the kernels compute the factors
+    static constexpr size_t kChirpTableCap = (size_t)1 << 30;
+    int add_chirp(int64_t s, cudaStream_t st) {
+        const ChirpParams<C> cp = chirp(s, 0);
+        if (cp.mode != PRE_CHIRP || cp.tab) return DGT_OK;
+        size_t have = 0;
+        for (auto& kv : chirpt) have += kv.second.bytes;
+        const size_t bytes = sizeof(C) * (size_t)core.L;
+        if (have + bytes > kChirpTableCap) return DGT_OK;
+        DevBuf& b = chirpt[cp.s_2L];
+        DGT_TRY(b.alloc(bytes));
+        CUDA_TRY(launch_chirp_table<T>(cp, (C*)b.p, st));
+        return DGT_OK;
     }
     ChirpParams<C> nochirp() const {
         ChirpParams<C> cp{};
@@ -573,6 +593,10 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         DGT_TRY(make_cis(cis2L, 2 * k.L, st));
         DGT_TRY(make_cis(cis2N, 2 * k.N, st));
         DGT_TRY(make_cis(cisLM, k.lam2 * k.M, st));
+        if (k.route == DGT_ROUTE_SHEAR) {
+            DGT_TRY(add_chirp(k.sh.s1, st));
+            if (k.freq_shear) DGT_TRY(add_chirp(-k.sh.s0, st));
+        }
         // coset shifts sigma_j = j s mod b (Prop. mwindec)
         std::vector<int64_t> sg(k.lam2);
         for (int64_t j = 0; j < k.lam2; ++j) sg[j] = (j * k.s) % k.b;
