@@ -732,6 +732,26 @@ __global__ void __launch_bounds__(AnaCfg<N>::THREADS, sizeof(T) == 4 ? AnaCfg<N>
     const bool ok = P0 + gi < pairs_total;
     const int Lg = (int)fp.Lg;
     const bool dh = (n1 * fp.lam1) % lam2 != 0;                 // delta = 1/2 (uniform per group)
+    // L2 prefetch of the segment of the CTA kAnaAhead CTAs later, so that its staging loads
+    // find the signal in L2 (one prefetch per 128-byte line, every address inside its signal)
+    {
+        constexpr int kAnaAhead = 256;
+        const int64_t Pn = P0 + (int64_t)kAnaAhead * RC::RPB;
+        if (Pn < pairs_total) {
+            const int64_t bn = Pn / half;
+            const int64_t pn = Pn - bn * half;
+            int64_t ln = fp.a * ((pn / lam2) * 2 * lam2) - fp.center;
+            if (ln < 0) ln += fp.L;
+            const int S = (2 * RC::RPB - 1) * (int)fp.a + Lg;
+            constexpr int PER = 128 / (int)sizeof(T);
+            const T* fn = f + bn * fp.L;
+            for (int i = threadIdx.x * PER; i < S; i += RC::THREADS * PER) {
+                int64_t l = ln + i;
+                if (l >= fp.L) l -= fp.L;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(fn + l));
+            }
+        }
+    }
     // segment of the CTA: samples ln(nmin) + i, i < S; eight loads in flight per thread
     {
         const int S = (2 * RC::RPB - 1) * (int)fp.a + Lg;
