@@ -287,10 +287,34 @@ int dgt_profile_stop(char* json, size_t cap);
  * FMA, 2 double FMA.  Synchronises `stream`; allocates 4 bytes. */
 int dgt_fma_rate(int kind, double* flops_per_s, void* stream);
 
-/* Building block check: `howmany` contiguous complex transforms of length n (device buffers),/* Building block check: `howmany` contiguous complex transforms of length n (device buffers),
+/* Building block check: `howmany` contiguous complex transforms of length n (device buffers),
  * direction -1 (forward) or +1 (unnormalised inverse), precision DGT_F32 / DGT_F64. */
 int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, void* out, int64_t howmany,
                      void* stream);
+
+/* Bounds checking (no counterpart in the paper; a checking aid, not a step of the method).
+ * A library compiled with -DDGT_DEBUG (libdgt_debug.so, selected in Python by DGT_DEBUG=1)
+ * surrounds every device allocation it makes with 4096-byte guard zones of 0xFF bytes (a NaN
+ * in float32 and float64), puts such zones between the regions of each analysis / synthesis
+ * workspace (the plan's or the caller's, whose dgt_workspace_bytes grows accordingly), and
+ * after every kernel launch checks every zone on the launching stream: an overwritten word
+ * counts as a violation and is restored; nothing traps.  Out-of-bounds reads of a zone load
+ * NaNs into the results.  That build serialises analysis / synthesis calls, synchronises the
+ * device at the end of each and must not be captured into a CUDA graph; the caller's own
+ * input and output buffers are not guarded.
+ *
+ * dgt_debug_build: 1 in the DGT_DEBUG build, else 0.
+ * dgt_debug_status: synchronises the device; *violations = guard words found overwritten
+ * since the previous call (then cleared); for the first of them, kernel (kernel_len bytes,
+ * NUL-terminated; may be NULL) receives the name of the launch after which it was found and
+ * *zone_offset its byte offset inside its guard zone (-1 when there is none).  Returns
+ * DGT_ERR_UNSUPPORTED in the release build (nothing is checked there).
+ * dgt_debug_touch_guard: overwrites the first word of the trailing guard zone of one of the
+ * plan's allocations (memory the library owns), so that a test can see the next launch's
+ * check report it.  DGT_ERR_UNSUPPORTED in the release build. */
+int dgt_debug_build(void);
+int dgt_debug_status(unsigned long long* violations, long long* zone_offset, char* kernel, size_t kernel_len);
+int dgt_debug_touch_guard(dgt_plan_t plan);
 
 #ifdef __cplusplus
 }

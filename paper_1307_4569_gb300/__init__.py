@@ -4,5 +4,5 @@ The compute path is libdgt.so (hand-written CUDA behind the C ABI in include/dgt
 this package holds its sources (csrc/), the in-tree build (build.py), the ctypes
 binding (_capi.py), the PyTorch-facing API (api.py) and the serving loop (serve.py).
 """
-from .api import DGTFunction, LogMagLoss, Plan, Plan2, dgt, fft_selftest, log_magnitude_loss  # noqa: F401
+from .api import DGTFunction, LogMagLoss, Plan, Plan2, debug_status, dgt, fft_selftest, log_magnitude_loss  # noqa: F401
 from ._capi import DGTError  # noqa: F401

@@ -10,7 +10,8 @@ import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libdgt.so")
+# DGT_DEBUG=1 selects the guard-zone bounds-checking build (build.build(debug=True))
+LIB_PATH = os.path.join(HERE, "lib", "libdgt_debug.so" if os.environ.get("DGT_DEBUG") == "1" else "libdgt.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "dgt.h")
 
 DGT_OK, DGT_ERR_ARG, DGT_ERR_LENGTH, DGT_ERR_NOT_FRAME, DGT_ERR_CUDA, DGT_ERR_OOM, DGT_ERR_TIMEOUT, \
@@ -79,6 +80,9 @@ SIGNATURES = {
     "dgt_last_error": (C.c_char_p, []),
     "dgt_fft_selftest": (i32, [i64, i32, i32, vp, vp, i64, vp]),
     "dgt_fma_rate": (i32, [i32, C.POINTER(C.c_double), vp]),
+    "dgt_debug_build": (i32, []),
+    "dgt_debug_status": (i32, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_longlong), C.c_char_p, C.c_size_t]),
+    "dgt_debug_touch_guard": (i32, [vp]),
     "dgt_profile_start": (i32, []),
     "dgt_profile_stop": (i32, [C.c_char_p, C.c_size_t]),
 }

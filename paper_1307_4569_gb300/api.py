@@ -291,6 +291,17 @@ class Plan2:
         K.check(K.lib().dgt2_plan_status(self._h, _stream(stream)))
 
 
+def debug_status():
+    """Guard-zone report of the DGT_DEBUG build (``DGT_DEBUG=1`` loads libdgt_debug.so):
+    (violations, kernel, zone_offset) -- guard words found overwritten since the previous call,
+    the launch after which the first was found and its byte offset in its zone.  Synchronises
+    the device.  Raises DGTError (DGT_ERR_UNSUPPORTED) in the release build."""
+    v, off = C.c_ulonglong(0), C.c_longlong(-1)
+    name = C.create_string_buffer(128)
+    K.check(K.lib().dgt_debug_status(C.byref(v), C.byref(off), name, 128))
+    return int(v.value), name.value.decode(), int(off.value)
+
+
 def fft_selftest(x: torch.Tensor, direction: int = -1) -> torch.Tensor:
     """Library FFT building block on rows of x (contiguous complex CUDA tensor)."""
     prec = K.F64 if x.dtype == torch.complex128 else K.F32

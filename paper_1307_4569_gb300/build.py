@@ -3,6 +3,10 @@
 Each translation unit is compiled in parallel, then linked into
 ``paper_1307_4569_gb300/lib/libdgt.so``.  Rebuilds only when a source or header is
 newer than the library.  No CMake, no torch extension machinery.
+
+``build(debug=True)`` compiles the same sources with ``-DDGT_DEBUG`` into
+``lib/libdgt_debug.so`` (guard-zone bounds checking after every launch, include/dgt.h);
+the binding loads it instead of the release library when ``DGT_DEBUG=1``.
 """
 from __future__ import annotations
 
@@ -18,8 +22,10 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "lib", "obj")
 LIB = os.path.join(LIBDIR, "libdgt.so")
+LIB_DEBUG = os.path.join(LIBDIR, "libdgt_debug.so")
+OBJDIR_DEBUG = os.path.join(HERE, "lib", "obj_debug")
 SOURCES = ["engine_zak.cu", "engine_aux.cu", "plan.cu", "p2_cols_f32.cu", "p2_rows_f32.cu", "p2_cols_f64.cu",
-           "p2_rows_f64.cu", "mr_f32.cu", "mr_f64.cu"]
+           "p2_rows_f64.cu", "mr_f32.cu", "mr_f64.cu", "debug.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,23 +42,29 @@ def _deps() -> list[str]:
     return out
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    objdir = OBJDIR_DEBUG if debug else OBJDIR
+    if not force and up_to_date(debug):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
              "-I", os.path.join(ROOT, "include"), "-I", CSRC] + ARCH + (extra_flags or [])
+    if debug:
+        flags.append("-DDGT_DEBUG")
 
     def one(src):
-        obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,14 +75,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

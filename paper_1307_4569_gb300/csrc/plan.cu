@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/dgt.h"
+#include "debug.h"
 #include "engine.h"
 
 using namespace dgt;
@@ -82,6 +83,7 @@ static cudaEvent_t prof_event() {
             cudaEventRecord(_ka, ST);                                 \
         }                                                             \
         CUDA_TRY(__VA_ARGS__);                                        \
+        if (kDebug) dbg_after_launch(NAME, ST);                       \
         if (g_prof_on) {                                              \
             cudaEventRecord(_kb, ST);                                 \
             g_prof.push_back({NAME, _ka, _kb});                       \
@@ -231,12 +233,12 @@ struct DevBuf {
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    ~DevBuf() { if (p) cudaFree(p); }
+    ~DevBuf() { dbg_free(p); }
     int alloc(size_t n) {
         if (n <= bytes && p) return DGT_OK;
-        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        if (p) { dbg_free(p); p = nullptr; bytes = 0; }
         if (n == 0) return DGT_OK;
-        cudaError_t e = cudaMalloc(&p, n);
+        cudaError_t e = dbg_malloc(&p, n);
         if (e != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
@@ -372,6 +374,8 @@ struct dgt_plan_s {
                             cudaStream_t st) = 0;
     virtual int logmag(const void* c, void* G, double* loss, double eps, int64_t B, cudaStream_t st) = 0;
     virtual int fir_synthesis_noalloc(const void* c, void* f, int f_real, int64_t B, int which, cudaStream_t st) = 0;
+    // DGT_DEBUG build: damage the trailing guard zone of one of the plan's allocations
+    virtual int debug_touch_guard() { return DGT_ERR_UNSUPPORTED; }
     // synchronise st; a pending CUDA error, or an expired wait of this plan's own calls
     int status_check(cudaStream_t st) {
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -436,6 +440,10 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     DevBuf lossparts;
     DevBuf hbtab;                      // FIR route, lambda2 = 2: exp(-pi i k / M), k < M (real-input pairing)
     std::map<int64_t, DevBuf> chirpt;  // shear routes: s mod 2L -> pchirp(L, s)(l), l < L
+
+    int debug_touch_guard() override {
+        return sigma.p ? dbg_touch_trailing_guard(sigma.p, sigma.bytes) : DGT_ERR_UNSUPPORTED;
+    }
     DevBuf gradws;                     // work arrays of the window gradient
 
     const FftRef* fft(int64_t n) {
@@ -459,31 +467,47 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     }
 
     // ---- workspace layout -----------------------------------------------------------
+    // regions of the workspace; the DGT_DEBUG build puts a guard zone before, between and after
+    // them (guard[0..ng)), checked after every launch of the call
     struct Layout {
         size_t zf, y, tmp, fh, seams, total;
+        size_t guard[5];
+        int ng;
     };
     static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
     Layout layout(int64_t B) const {
         const PlanCore& k = core;
         Layout ly{};
         size_t off = 0;
+        auto gz = [&]() {
+            if (kDebug) {
+                ly.guard[ly.ng++] = off;
+                off += kGuard;
+            }
+        };
+        gz();
         if (k.route == DGT_ROUTE_FIR) {
             FirParams<C> fp{};
             fp.N = k.N; fp.cols = k.fir_cols; fp.Lg = k.Lg; fp.a = k.a;
             ly.seams = off;
             off += al(sizeof(C) * (size_t)B * fir_seam_elems(fp));
+            gz();
             ly.total = off;
             return ly;
         }
         ly.zf = off;
         off += al(sizeof(C) * (size_t)B * k.L);
+        gz();
         ly.y = off;
         off += al(sizeof(C) * (size_t)B * k.J * k.sep.d * k.sep.q * k.sep.M);
+        gz();
         if (k.freq_shear) {
             ly.tmp = off;
             off += al(sizeof(C) * (size_t)B * k.L);
+            gz();
             ly.fh = off;
             off += al(sizeof(C) * (size_t)B * k.L);
+            gz();
         }
         ly.total = off;
         return ly;
@@ -525,7 +549,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         if (have + bytes > kChirpTableCap) return DGT_OK;
         DevBuf& b = chirpt[cp.s_2L];
         DGT_TRY(b.alloc(bytes));
-        CUDA_TRY(launch_chirp_table<T>(cp, (C*)b.p, st));
+        KTRY("chirp_table", st, launch_chirp_table<T>(cp, (C*)b.p, st));
         return DGT_OK;
     }
     ChirpParams<C> nochirp() const {
@@ -626,7 +650,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         std::vector<double> gh = k.g_host;
         DGT_TRY(upload_cplx<double>(g64, gh, st));
         DGT_TRY(gT.alloc(sizeof(C) * n));
-        CUDA_TRY(launch_convert<double, T>(g64.p, 0, (C*)gT.p, n, st));
+        KTRY("convert", st, launch_convert<double, T>(g64.p, 0, (C*)gT.p, n, st));
         DGT_TRY(build_factor(0, (const C*)gT.p, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         return DGT_OK;
@@ -653,18 +677,18 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         const FftRef* fd = fft(k.sep.d);
         if (k.route == DGT_ROUTE_COSET) {
             DGT_TRY(tmpwin.alloc(sizeof(C) * (size_t)k.J * k.L));
-            CUDA_TRY(launch_coset_windows<T>(gw, (C*)tmpwin.p, k.L, k.a, k.J, (const int64_t*)sigma.p, cisL.tab, st));
-            CUDA_TRY(launch_zak_fwd<T>(tmpwin.p, 0, k.L, out, k.L, k.L, k.sep.d, *fd, nochirp(), k.J, st));
+            KTRY("coset_windows", st, launch_coset_windows<T>(gw, (C*)tmpwin.p, k.L, k.a, k.J, (const int64_t*)sigma.p, cisL.tab, st));
+            KTRY("zak_fwd", st, launch_zak_fwd<T>(tmpwin.p, 0, k.L, out, k.L, k.L, k.sep.d, *fd, nochirp(), k.J, st));
         } else if (!k.freq_shear) {
-            CUDA_TRY(launch_zak_fwd<T>(gw, 0, k.L, out, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 0), 1, st));
+            KTRY("zak_fwd", st, launch_zak_fwd<T>(gw, 0, k.L, out, k.L, k.L, k.sep.d, *fd, chirp(k.sh.s1, 0), 1, st));
         } else {
             // g^ = pchirp(L, -s0) FFT(pchirp(L, s1) g) / L   (Algorithm 1, frequency-shear branch)
             DGT_TRY(tmpwin.alloc(sizeof(C) * 2 * (size_t)k.L));
             C* t1 = (C*)tmpwin.p;
             C* t2 = t1 + k.L;
-            CUDA_TRY(launch_fftL_cols<T>(gw, 0, t1, k.L1, k.L2, -1, *fft(k.L1), chirp(k.sh.s1, 0), cisL.tab, 1, st));
-            CUDA_TRY(launch_fftL_rows<T>(t1, t2, 0, k.L1, k.L2, -1, *fft(k.L2), chirp(-k.sh.s0, 0), (T)1 / (T)k.L, 1, st));
-            CUDA_TRY(launch_zak_fwd<T>(t2, 0, k.L, out, k.L, k.L, k.sep.d, *fd, nochirp(), 1, st));
+            KTRY("fftL_cols", st, launch_fftL_cols<T>(gw, 0, t1, k.L1, k.L2, -1, *fft(k.L1), chirp(k.sh.s1, 0), cisL.tab, 1, st));
+            KTRY("fftL_rows", st, launch_fftL_rows<T>(t1, t2, 0, k.L1, k.L2, -1, *fft(k.L2), chirp(-k.sh.s0, 0), (T)1 / (T)k.L, 1, st));
+            KTRY("zak_fwd", st, launch_zak_fwd<T>(t2, 0, k.L, out, k.L, k.L, k.sep.d, *fd, nochirp(), 1, st));
         }
         zg_ok[slot] = true;
         return DGT_OK;
@@ -673,15 +697,15 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     int build_fir_mt(int slot, const double2* taps64, cudaStream_t st) {
         const PlanCore& k = core;
         DGT_TRY(firmt[slot].alloc(sizeof(C) * (size_t)k.lam2 * k.Lg));
-        CUDA_TRY(launch_fir_modtaps<T>(taps64, (C*)firmt[slot].p, k.Lg, k.lam2, k.M, st));
+        KTRY("fir_modtaps", st, launch_fir_modtaps<T>(taps64, (C*)firmt[slot].p, k.Lg, k.lam2, k.M, st));
         return DGT_OK;
     }
 
     int set_window(const void* g, int is_real, cudaStream_t st) override {
         const PlanCore& k = core;
         const int64_t n = k.win_kind == DGT_WINDOW_FIR ? k.Lg : k.L;
-        CUDA_TRY(launch_convert<T, T>(g, is_real, (C*)gT.p, n, st));
-        CUDA_TRY(launch_convert<T, double>(g, is_real, (double2*)g64.p, n, st));
+        KTRY("convert", st, launch_convert<T, T>(g, is_real, (C*)gT.p, n, st));
+        KTRY("convert", st, launch_convert<T, double>(g, is_real, (double2*)g64.p, n, st));
         core.win_real = is_real;
         zg_ok[1] = zg_ok[2] = false;
         return build_factor(0, (const C*)gT.p, st);
@@ -708,6 +732,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             DGT_TRY(work.alloc(ly.total));
             ws = (char*)work.p;
         }
+        DbgScope dbg(st, ws, ly.guard, ly.ng);
         if (k.route == DGT_ROUTE_FIR) {
             FirParams<C> fp = fir_params(0);
             fp.half = half;
@@ -772,11 +797,11 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             // short window: S is diagonal; gamma has the same support
             DevBuf g64o;
             DGT_TRY(g64o.alloc(sizeof(double2) * k.Lg));
-            CUDA_TRY(launch_fir_dual((const double2*)g64.p, (double2*)g64o.p, k.Lg, k.a, k.M, tight, (int*)status.p, st));
+            KTRY("fir_dual", st, launch_fir_dual((const double2*)g64.p, (double2*)g64o.p, k.Lg, k.a, k.M, tight, (int*)status.p, st));
             DGT_TRY(check_status(st));
             if (k.route == DGT_ROUTE_FIR) {
                 DGT_TRY(gam[which].alloc(sizeof(C) * k.Lg));
-                CUDA_TRY(launch_convert<double, T>(g64o.p, 0, (C*)gam[which].p, k.Lg, st));
+                KTRY("convert", st, launch_convert<double, T>(g64o.p, 0, (C*)gam[which].p, k.Lg, st));
                 DGT_TRY(build_fir_mt(which, (const double2*)g64o.p, st));
                 zg_ok[which] = true;
                 CUDA_TRY(cudaStreamSynchronize(st));
@@ -816,18 +841,18 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         DGT_TRY(zj.alloc(sizeof(double2) * (size_t)k.lam2 * k.L));
         DGT_TRY(zo.alloc(sizeof(double2) * (size_t)k.L));
         DGT_TRY(gout.alloc(sizeof(double2) * (size_t)k.L));
-        CUDA_TRY(launch_coset_windows<double>((const double2*)g64.p, (double2*)gj.p, k.L, k.a, k.lam2,
+        KTRY("coset_windows", st, launch_coset_windows<double>((const double2*)g64.p, (double2*)gj.p, k.L, k.a, k.lam2,
                                               (const int64_t*)sigma.p, cisL64.tab, st));
         ChirpParams<double2> none{};
         none.mode = PRE_NONE;
         none.L = k.L;
-        CUDA_TRY(launch_zak_fwd<double>(gj.p, 0, k.L, (double2*)zj.p, k.L, k.L, cg.d, twd.ref, none, k.lam2, st));
-        CUDA_TRY(launch_gram_solve((const double2*)zj.p, k.lam2, (double2*)zo.p, cg, tight, (int*)status.p, st));
+        KTRY("zak_fwd", st, launch_zak_fwd<double>(gj.p, 0, k.L, (double2*)zj.p, k.L, k.L, cg.d, twd.ref, none, k.lam2, st));
+        KTRY("gram_solve", st, launch_gram_solve((const double2*)zj.p, k.lam2, (double2*)zo.p, cg, tight, (int*)status.p, st));
         DGT_TRY(check_status(st));
-        CUDA_TRY(launch_zak_inv<double>((const double2*)zo.p, k.L, gout.p, 0, k.L, k.L, cg.d, twd.ref, none,
+        KTRY("zak_inv", st, launch_zak_inv<double>((const double2*)zo.p, k.L, gout.p, 0, k.L, k.L, cg.d, twd.ref, none,
                                         1.0 / (double)cg.d, 1, st));
         DGT_TRY(gam[which].alloc(sizeof(C) * k.L));
-        CUDA_TRY(launch_convert<double, T>(gout.p, 0, (C*)gam[which].p, k.L, st));
+        KTRY("convert", st, launch_convert<double, T>(gout.p, 0, (C*)gam[which].p, k.L, st));
         DGT_TRY(build_factor(which, (const C*)gam[which].p, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         return DGT_OK;
@@ -853,10 +878,10 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         const int64_t n = fir ? k.Lg : k.L;
         zg_ok[3] = false;
         DGT_TRY(gam[3].alloc(sizeof(C) * n));
-        CUDA_TRY(launch_convert<T, T>(gamma, gamma_real, (C*)gam[3].p, n, st));
+        KTRY("convert", st, launch_convert<T, T>(gamma, gamma_real, (C*)gam[3].p, n, st));
         if (fir) {
             DGT_TRY(tmpwin.alloc(sizeof(double2) * n));
-            CUDA_TRY(launch_convert<T, double>(gamma, gamma_real, (double2*)tmpwin.p, n, st));
+            KTRY("convert", st, launch_convert<T, double>(gamma, gamma_real, (double2*)tmpwin.p, n, st));
             DGT_TRY(build_fir_mt(3, (const double2*)tmpwin.p, st));
             zg_ok[3] = true;
         } else {
@@ -879,6 +904,7 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
             DGT_TRY(work.alloc(ly.total));
             ws = (char*)work.p;
         }
+        DbgScope dbg(st, ws, ly.guard, ly.ng);
         if (k.route == DGT_ROUTE_FIR) {
             if (!k.fir_synth_ok)
                 return fail(DGT_ERR_UNSUPPORTED, "FIR synthesis: %lld columns per tile cannot cover a window of %lld",
@@ -1613,6 +1639,13 @@ int dgt_plan_status(dgt_plan_t plan, void* stream) {
     return plan->status_check((cudaStream_t)stream);
 }
 
+int dgt_debug_touch_guard(dgt_plan_t plan) {
+    if (!plan) return fail(DGT_ERR_ARG, "null plan");
+    const int r = plan->debug_touch_guard();
+    if (r == DGT_ERR_UNSUPPORTED) return fail(r, "guard zones exist only in the DGT_DEBUG build");
+    return r == DGT_OK ? DGT_OK : fail(r, "could not write the guard zone");
+}
+
 int dgt_sync(void* stream) {
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     CUDA_TRY(cudaGetLastError());
@@ -1713,7 +1746,7 @@ int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, vo
             return fail(DGT_ERR_UNSUPPORTED, "length %lld", (long long)n);
         DGT_TRY(upload_cplx<float>(t.buf, twiddle_host(n), st));
         t.ref.tw = t.buf.p;
-        CUDA_TRY(launch_fft_rows_test<float>((const float2*)in, (float2*)out, t.ref, direction, howmany, st));
+        KTRY("fft_rows_test", st, launch_fft_rows_test<float>((const float2*)in, (float2*)out, t.ref, direction, howmany, st));
         CUDA_TRY(cudaStreamSynchronize(st));
     } else {
         TwTable<double> t;
@@ -1721,7 +1754,7 @@ int dgt_fft_selftest(int64_t n, int precision, int direction, const void* in, vo
             return fail(DGT_ERR_UNSUPPORTED, "length %lld", (long long)n);
         DGT_TRY(upload_cplx<double>(t.buf, twiddle_host(n), st));
         t.ref.tw = t.buf.p;
-        CUDA_TRY(launch_fft_rows_test<double>((const double2*)in, (double2*)out, t.ref, direction, howmany, st));
+        KTRY("fft_rows_test", st, launch_fft_rows_test<double>((const double2*)in, (double2*)out, t.ref, direction, howmany, st));
         CUDA_TRY(cudaStreamSynchronize(st));
     }
     return DGT_OK;

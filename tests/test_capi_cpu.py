@@ -1,6 +1,7 @@
 """The C-ABI library builds, loads and exports every entry point of include/dgt.h (no GPU)."""
 import ctypes
 import os
+import subprocess
 
 import pytest
 
@@ -35,6 +36,24 @@ def test_binding_loads_and_reports_errors(libpath):
     assert lib.dgt_strerror(99) == b"DGT_ERR_UNKNOWN"
     with pytest.raises(K.DGTError):
         K.check(K.DGT_ERR_ARG)
+
+
+def test_release_build_reports_no_guard_checks(libpath):
+    # the guard-zone entry points exist in the release build and say that nothing is checked
+    lib = K.lib()
+    assert lib.dgt_debug_build() == 0
+    v, off, name = ctypes.c_ulonglong(5), ctypes.c_longlong(0), ctypes.create_string_buffer(16)
+    assert lib.dgt_debug_status(ctypes.byref(v), ctypes.byref(off), name, 16) == K.DGT_ERR_UNSUPPORTED
+    assert v.value == 0 and off.value == -1 and name.value == b""
+    assert lib.dgt_debug_touch_guard(None) == K.DGT_ERR_ARG
+
+
+def test_debug_guard_code_compiles(tmp_path):
+    # the DGT_DEBUG-only translation unit (zone registry, check kernel, status) cross-compiles
+    cmd = [B._nvcc(), "-c", os.path.join(B.CSRC, "debug.cu"), "-o", str(tmp_path / "debug.o"), "-O3", "-std=c++17",
+           "-Xcompiler", "-fPIC", "-I", os.path.join(B.ROOT, "include"), "-I", B.CSRC, "-DDGT_DEBUG"] + B.ARCH
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
 
 
 def test_build_is_incremental(libpath):
