@@ -128,6 +128,7 @@ template <typename C> struct FirParams {
     // the definition splits into this tap factor and the column constant
     // exp(-2 pi i ln wn / (lam2 M)), applied once per column after (before) the FFT.
     const C* mtaps;
+    const typename RealOf<C>::type* rtaps;   // Re mtaps[0][.], dense (Lg values)
     ModU64 mN;                        // division by N (row = b N + n)
     int64_t cols;                     // time positions per CTA
     int64_t group;                    // rows transformed at once (spare buffer rows)

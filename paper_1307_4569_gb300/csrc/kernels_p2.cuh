@@ -782,17 +782,17 @@ __global__ void __launch_bounds__(AnaCfg<N>::THREADS, sizeof(T) == 4 ? AnaCfg<N>
     const int lnm1 = (int)(ln1 & (N - 1)), lnm2 = (int)(ln2 & (N - 1));
     const T* s1 = seg + (n1 - nmin) * fp.a;
     const T* s2 = seg + (n2 - nmin) * fp.a;
-    const C* h = fp.mtaps;                                      // row wn = 0: the real taps
+    const T* h = fp.rtaps;                                      // the real taps, dense
     C v[16];
     fft_p2<N, -1, 1>(0, t, sm, tw, [&](int k) -> C {
         const int tap1 = (k - lnm1) & (N - 1), tap2 = (k - lnm2) & (N - 1);
         T x1 = (T)0, x2 = (T)0;
         if (tap1 < Lg) {
-            x1 = s1[tap1] * __ldg(&h[tap1].x);
+            x1 = s1[tap1] * __ldg(h + tap1);
             if (dh && k < lnm1) x1 = -x1;
         }
         if (tap2 < Lg) {
-            x2 = s2[tap2] * __ldg(&h[tap2].x);
+            x2 = s2[tap2] * __ldg(h + tap2);
             if (dh && k < lnm2) x2 = -x2;
         }
         C z = mk(x1, x2);
@@ -968,8 +968,8 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_pair_p2
     const int S = a * (nc - 1) + Lg;
     const int D = (Lg + a - 1) / a;
     const int PR = nc / D;                           // columns per round
-    // the real taps: row wn = 0 of the modulated taps (real parts), read through L1
-    const T* h = reinterpret_cast<const T*>(fp.mtaps);
+    // the real taps (real parts of row wn = 0 of the modulated taps, dense), read through L1
+    const T* h = fp.rtaps;
     for (int i = threadIdx.x; i < S; i += RC::THREADS) acc[i] = (T)0;
     __syncthreads();
     for (int dq = 0; dq < D / 2; ++dq) {
@@ -1039,7 +1039,7 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_pair_p2
                 for (int i = 0; i < 16; ++i) {
                     const int k = p2_out_pos<N>(t, i);
                     const int tap = (k - lnm1) & (N - 1);
-                    if (tap < Lg) ar[tap] += ((dh && k < lnm1) ? -sg1 : sg1) * __ldg(h + 2 * tap) * v[i].x;
+                    if (tap < Lg) ar[tap] += ((dh && k < lnm1) ? -sg1 : sg1) * __ldg(h + tap) * v[i].x;
                 }
             }
             __syncthreads();                        // columns of the rounds q and q + lambda2 overlap
@@ -1049,7 +1049,7 @@ __global__ void __launch_bounds__(SynCfg<N, DIV>::THREADS) fir_synthesis_pair_p2
                 for (int i = 0; i < 16; ++i) {
                     const int k = p2_out_pos<N>(t, i);
                     const int tap = (k - lnm2) & (N - 1);
-                    if (tap < Lg) ar[tap] += ((dh && k < lnm2) ? -sg2 : sg2) * __ldg(h + 2 * tap) * v[i].y;
+                    if (tap < Lg) ar[tap] += ((dh && k < lnm2) ? -sg2 : sg2) * __ldg(h + tap) * v[i].y;
                 }
             }
             __syncthreads();
@@ -1260,7 +1260,7 @@ cudaError_t p2_fir_analysis_n(const void* f, int f_real, cplx<T>* c, const FirPa
         // real-input pairing: real signal and window, lambda2 <= 2, whole CTAs of pairs
         const int64_t S2 = (2 * RC::RPB - 1) * fp.a + fp.Lg;
         const size_t seg2 = sizeof(T) * (size_t)S2;
-        if (f_real && fp.pairable && fp.lam2 <= 2 && RC::RPB % fp.lam2 == 0 && fp.Lg <= N &&
+        if (f_real && fp.pairable && fp.rtaps && fp.lam2 <= 2 && RC::RPB % fp.lam2 == 0 && fp.Lg <= N &&
             fp.N % (2 * RC::RPB) == 0 && S2 <= fp.L && smem + seg2 <= kSmemBudget && (fp.lam2 == 1 || fp.hb)) {
             auto k = fir_analysis_pair_p2<T, N>;
             cudaError_t e = p2_smem(k, smem + seg2);
@@ -1353,7 +1353,7 @@ cudaError_t p2_fir_synthesis_n(const cplx<T>* c, void* f, int f_real, cplx<T>* s
     {
         // real output, real window, lambda2 <= 2, rounds that pair up (D a multiple of 2 lambda2)
         const int64_t D = (fp.Lg + fp.a - 1) / fp.a;
-        if (f_real && fp.pairable && fp.lam2 <= 2 && fp.Lg <= N && D % (2 * fp.lam2) == 0 && fp.cols % D == 0 &&
+        if (f_real && fp.pairable && fp.rtaps && fp.lam2 <= 2 && fp.Lg <= N && D % (2 * fp.lam2) == 0 && fp.cols % D == 0 &&
             fp.N % fp.cols == 0 && (fp.lam2 == 1 || fp.hb)) {
             cudaError_t e = cudaErrorNotSupported;
             if (p2_fir_synthesis_small<T, N>(fp.cols, fp.N, fp.a, fp.Lg))

@@ -694,10 +694,15 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         return DGT_OK;
     }
 
+    // [lam2][Lg] modulated taps, then the Lg real parts of row 0 (the taps themselves for a real
+    // window) as a dense array for the paired kernels
     int build_fir_mt(int slot, const double2* taps64, cudaStream_t st) {
         const PlanCore& k = core;
-        DGT_TRY(firmt[slot].alloc(sizeof(C) * (size_t)k.lam2 * k.Lg));
+        const size_t mt = sizeof(C) * (size_t)k.lam2 * k.Lg;
+        DGT_TRY(firmt[slot].alloc(mt + sizeof(T) * (size_t)k.Lg));
         KTRY("fir_modtaps", st, launch_fir_modtaps<T>(taps64, (C*)firmt[slot].p, k.Lg, k.lam2, k.M, st));
+        CUDA_TRY(cudaMemcpy2DAsync((char*)firmt[slot].p + mt, sizeof(T), firmt[slot].p, sizeof(C), sizeof(T),
+                                   (size_t)k.Lg, cudaMemcpyDeviceToDevice, st));
         return DGT_OK;
     }
 
@@ -776,6 +781,8 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
         fp.Lg = k.Lg; fp.center = k.center; fp.cisLM = cisLM.tab; fp.cols = k.fir_cols;
         fp.taps = which == 0 ? (const C*)gT.p : (const C*)gam[which].p;
         fp.mtaps = (const C*)firmt[which].p;
+        fp.rtaps = firmt[which].p ? (const T*)((const char*)firmt[which].p + sizeof(C) * (size_t)k.lam2 * k.Lg)
+                                  : nullptr;
         fp.mN = make_mod((uint64_t)k.N);
         fp.group = k.fir_group;
         fp.pairable = which <= 2 && k.win_real;
