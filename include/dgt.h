@@ -266,6 +266,13 @@ int dgt_workspace_status(dgt_plan_t plan, const void* workspace, void* stream);
  * limit.  Host-global: it applies to every plan of the process. */
 long long dgt_wait_limit(long long cycles);
 
+/* The largest total size in bytes of the chirp tables that a shear-route plan created later
+ * keeps (Algorithm 1's pchirp factors, one table of L complex values per chirp, computed from
+ * the exact integer exponent; default 2^30).  A plan whose tables would exceed it computes the
+ * factors per sample instead, with bit-identical results.  bytes < 0 only queries.  Returns the
+ * previous cap.  Host-global. */
+long long dgt_chirp_table_cap(long long bytes);
+
 /* Release the plan and its device memory (synchronises the device first). */
 void dgt_plan_destroy(dgt_plan_t plan);
 

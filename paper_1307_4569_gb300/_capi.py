@@ -81,6 +81,7 @@ SIGNATURES = {
     "dgt_fft_selftest": (i32, [i64, i32, i32, vp, vp, i64, vp]),
     "dgt_fma_rate": (i32, [i32, C.POINTER(C.c_double), vp]),
     "dgt_debug_build": (i32, []),
+    "dgt_chirp_table_cap": (C.c_longlong, [C.c_longlong]),
     "dgt_debug_status": (i32, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_longlong), C.c_char_p, C.c_size_t]),
     "dgt_debug_touch_guard": (i32, [vp]),
     "dgt_profile_start": (i32, []),

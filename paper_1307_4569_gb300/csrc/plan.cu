@@ -35,6 +35,7 @@ static int fail(int status, const char* fmt, ...) {
 
 namespace dgt {
 long long g_wait_limit_cycles = kWaitCycles;
+long long g_chirp_cap = 1ll << 30;     // bytes of chirp tables a plan created later may hold
 }
 
 #define CUDA_TRY(...)                                                                                 \
@@ -538,15 +539,14 @@ template <typename T> struct PlanImpl final : dgt_plan_s {
     }
     // the chirps of Algorithm 1 (pchirp(L, s1), and pchirp(L, -s0) in the frequency-shear branch)
     // as tables of L values, so that a kernel reads each sample's factor in one load; none
-    // beyond kChirpTableCap bytes, where the kernels compute the factors
-    static constexpr size_t kChirpTableCap = (size_t)1 << 30;
+    // beyond g_chirp_cap bytes per plan, where the kernels compute the factors
     int add_chirp(int64_t s, cudaStream_t st) {
         const ChirpParams<C> cp = chirp(s, 0);
         if (cp.mode != PRE_CHIRP || cp.tab) return DGT_OK;
         size_t have = 0;
         for (auto& kv : chirpt) have += kv.second.bytes;
         const size_t bytes = sizeof(C) * (size_t)core.L;
-        if (have + bytes > kChirpTableCap) return DGT_OK;
+        if ((long long)(have + bytes) > g_chirp_cap) return DGT_OK;
         DevBuf& b = chirpt[cp.s_2L];
         DGT_TRY(b.alloc(bytes));
         KTRY("chirp_table", st, launch_chirp_table<T>(cp, (C*)b.p, st));
@@ -1663,6 +1663,12 @@ int dgt_sync(void* stream) {
     }
     if (n) return fail(DGT_ERR_TIMEOUT, "synthesis kernels of %d plans gave up waiting for their tile copies", n);
     return DGT_OK;
+}
+
+long long dgt_chirp_table_cap(long long bytes) {
+    const long long old = g_chirp_cap;
+    if (bytes >= 0) g_chirp_cap = bytes;
+    return old;
 }
 
 long long dgt_wait_limit(long long cycles) {

@@ -70,3 +70,14 @@ def test_wait_limit_hook_sets_queries_and_restores(libpath):
     assert lib.dgt_wait_limit(0) == 12345
     assert lib.dgt_wait_limit(default) == 0
     assert lib.dgt_wait_limit(-1) == default
+
+
+def test_chirp_table_cap_sets_queries_and_restores(libpath):
+    # host-side state only: the cap plans created later apply to their chirp tables
+    lib = K.lib()
+    default = lib.dgt_chirp_table_cap(-1)
+    assert default == 1 << 30
+    assert lib.dgt_chirp_table_cap(0) == default
+    assert lib.dgt_chirp_table_cap(-1) == 0
+    assert lib.dgt_chirp_table_cap(default) == 0
+    assert lib.dgt_chirp_table_cap(-1) == default
