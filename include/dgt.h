@@ -183,6 +183,22 @@ int idgt_exec_window(dgt_plan_t plan, const void* c, void* f, int f_real_out, in
 int dgt_exec_real(dgt_plan_t plan, const void* f, void* c, int64_t batch, void* stream);
 int idgt_exec_real(dgt_plan_t plan, const void* c, void* f, int64_t batch, int which_window, void* stream);
 
+/* As dgt_exec / idgt_exec (the same transforms, eq. (DGT) and its adjoint), with HOST
+ * buffers: f HOST [batch][L], c HOST [batch][N][M], in the layouts of dgt_exec / idgt_exec.
+ * The batch goes in chunks of `chunk` signals (0: the whole batch) through two plan-owned
+ * device staging slots.  The host-to-device copy of chunk i + 1 and the device-to-host copy of
+ * chunk i - 1 run on two plan-owned streams while chunk i is transformed on `stream`.  The
+ * call is ordered after earlier work on `stream`, and later work on `stream` waits for its last
+ * copy; with pinned (page-locked) host buffers it returns before the copies end, so
+ * synchronise `stream` before reading the output.  Pageable buffers work, with copies that
+ * block the host.  The staging slots grow to 2 chunks of input and output and stay with the
+ * plan.  One call at a time per plan.  Errors: DGT_ERR_ARG (null pointer, negative batch or
+ * chunk), and those of dgt_exec / idgt_exec. */
+int dgt_exec_host(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, int64_t chunk,
+                  void* stream);
+int idgt_exec_host(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
+                   int64_t chunk, void* stream);
+
 /* Workspace needed by dgt_exec_ws / idgt_exec_ws for `batch` signals, in bytes. */
 int dgt_workspace_bytes(dgt_plan_t plan, int64_t batch, size_t* bytes);
 

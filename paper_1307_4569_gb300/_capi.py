@@ -80,6 +80,8 @@ SIGNATURES = {
     "dgt_last_error": (C.c_char_p, []),
     "dgt_fft_selftest": (i32, [i64, i32, i32, vp, vp, i64, vp]),
     "dgt_fma_rate": (i32, [i32, C.POINTER(C.c_double), vp]),
+    "dgt_exec_host": (i32, [vp, vp, i32, vp, i64, i64, vp]),
+    "idgt_exec_host": (i32, [vp, vp, vp, i32, i64, i32, i64, vp]),
     "dgt_debug_build": (i32, []),
     "dgt_chirp_table_cap": (C.c_longlong, [C.c_longlong]),
     "dgt_debug_status": (i32, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_longlong), C.c_char_p, C.c_size_t]),

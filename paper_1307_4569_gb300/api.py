@@ -207,6 +207,36 @@ class Plan:
                                      workspace.data_ptr() if workspace is not None else None, _stream(stream)))
         return out
 
+    def dgt_host(self, f: torch.Tensor, out: torch.Tensor | None = None, chunk: int = 0, stream=None):
+        """Analysis of HOST signals f[..., L] into HOST coefficients (dgt_exec_host): chunks of
+        `chunk` signals are copied in, transformed and copied out on overlapping streams.  With
+        pinned tensors the call returns before the copies end; synchronise `stream` first."""
+        if f.is_cuda or not f.is_contiguous() or f.dtype not in (self.rdtype, self.cdtype):
+            raise TypeError("signal must be a contiguous host tensor of the plan precision")
+        if f.shape[-1] != self.L:
+            raise ValueError("signal length %d != L=%d" % (f.shape[-1], self.L))
+        B = int(np.prod(f.shape[:-1])) if f.dim() > 1 else 1
+        if out is None:
+            out = torch.empty(tuple(f.shape[:-1]) + (self.N, self.M), dtype=self.cdtype, pin_memory=f.is_pinned())
+        K.check(K.lib().dgt_exec_host(self._h, f.data_ptr(), int(not f.is_complex()), out.data_ptr(), B, int(chunk),
+                                      _stream(stream)))
+        return out
+
+    def idgt_host(self, c: torch.Tensor, window: str = "dual", real: bool = False, out=None, chunk: int = 0,
+                  stream=None):
+        """Synthesis from HOST coefficients c[..., N, M] into HOST signals (idgt_exec_host)."""
+        if c.is_cuda or not c.is_contiguous() or c.dtype != self.cdtype:
+            raise TypeError("coefficients must be a contiguous host %s tensor" % self.cdtype)
+        if tuple(c.shape[-2:]) != (self.N, self.M):
+            raise ValueError("coefficient shape %s != (N, M)=(%d, %d)" % (tuple(c.shape), self.N, self.M))
+        B = int(np.prod(c.shape[:-2])) if c.dim() > 2 else 1
+        if out is None:
+            out = torch.empty(tuple(c.shape[:-2]) + (self.L,), dtype=self.rdtype if real else self.cdtype,
+                              pin_memory=c.is_pinned())
+        K.check(K.lib().idgt_exec_host(self._h, c.data_ptr(), out.data_ptr(), int(real), B, _SYN[window],
+                                       int(chunk), _stream(stream)))
+        return out
+
     def status(self, stream=None) -> None:
         """Synchronise and raise DGTError(DGT_ERR_TIMEOUT) if a bounded device wait of this
         plan's calls without a caller workspace expired (the plan's next call raises it too)."""

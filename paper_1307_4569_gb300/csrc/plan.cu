@@ -357,8 +357,36 @@ struct PlanCore {
     int device = -1;                   // the CUDA device current at creation (owns the plan's memory)
 };
 
+// Streams, events and device staging slots of the host-buffer entry points (dgt_exec_host,
+// idgt_exec_host), created on first use
+struct HostPipe {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t start = nullptr, last = nullptr, done_in[2] = {}, done_exec[2] = {}, done_out[2] = {};
+    DevBuf src[2], dst[2];
+    HostPipe() = default;
+    HostPipe(const HostPipe&) = delete;
+    HostPipe& operator=(const HostPipe&) = delete;
+    ~HostPipe() {
+        for (cudaEvent_t* e : {&start, &last, &done_in[0], &done_in[1], &done_exec[0], &done_exec[1], &done_out[0],
+                               &done_out[1]})
+            if (*e) cudaEventDestroy(*e);
+        if (in) cudaStreamDestroy(in);
+        if (out) cudaStreamDestroy(out);
+    }
+    int init() {
+        if (in) return DGT_OK;
+        CUDA_TRY(cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking));
+        CUDA_TRY(cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&start, &last, &done_in[0], &done_in[1], &done_exec[0], &done_exec[1], &done_out[0],
+                               &done_out[1]})
+            CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        return DGT_OK;
+    }
+};
+
 struct dgt_plan_s {
     virtual ~dgt_plan_s() { expiry_word_give(expired); }
+    std::unique_ptr<HostPipe> host_pipe;   // host-buffer entry points
     PlanCore core;
     unsigned int* expired = nullptr;   // host-mapped expiry word of the calls without a caller workspace
     virtual int exec(const void* f, int f_real, void* c, int64_t B, void* ws, cudaStream_t st) = 0;
@@ -1441,6 +1469,55 @@ struct dgt2_plan_s {
 };
 
 // ---------------------------------------------------------------------------------------
+// host-buffer pipeline: the batch in chunks of `chunk` signals through two device staging
+// slots.  Chunk i is copied in on the pipe's input stream, transformed on the caller's stream
+// and copied out on the pipe's output stream, so the copies of chunks i + 1 and i - 1 overlap
+// the transform of chunk i.  A slot is refilled only after the transform of the chunk two
+// earlier has read it, and rewritten only after that chunk's copy out.  The whole call is
+// ordered after the caller's earlier work on `st`, and the caller's later work waits for the
+// last copy out.
+// ---------------------------------------------------------------------------------------
+static int host_pipeline(dgt_plan_t plan, const void* in_h, size_t bin, void* out_h, size_t bout, int64_t batch,
+                         int64_t chunk, cudaStream_t st,
+                         const std::function<int(const void*, void*, int64_t)>& run) {
+    if (batch <= 0) return batch == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
+    if (chunk < 0) return fail(DGT_ERR_ARG, "negative chunk");
+    DGT_TRY(plan->pending_expiry());
+    if (!plan->host_pipe) plan->host_pipe.reset(new HostPipe());
+    HostPipe& hp = *plan->host_pipe;
+    DGT_TRY(hp.init());
+    const int64_t ch = chunk > 0 && chunk < batch ? chunk : batch;
+    const int64_t nchunks = (batch + ch - 1) / ch;
+    const int slots = nchunks > 1 ? 2 : 1;
+    for (int s = 0; s < slots; ++s) {
+        DGT_TRY(hp.src[s].alloc(bin * (size_t)ch));
+        DGT_TRY(hp.dst[s].alloc(bout * (size_t)ch));
+    }
+    CUDA_TRY(cudaEventRecord(hp.start, st));
+    CUDA_TRY(cudaStreamWaitEvent(hp.in, hp.start, 0));
+    CUDA_TRY(cudaStreamWaitEvent(hp.out, hp.start, 0));
+    for (int64_t i = 0; i < nchunks; ++i) {
+        const int s = (int)(i & 1);
+        const int64_t nb = std::min(ch, batch - i * ch);
+        if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(hp.in, hp.done_exec[s], 0));
+        CUDA_TRY(cudaMemcpyAsync(hp.src[s].p, (const char*)in_h + (size_t)(i * ch) * bin, (size_t)nb * bin,
+                                 cudaMemcpyHostToDevice, hp.in));
+        CUDA_TRY(cudaEventRecord(hp.done_in[s], hp.in));
+        CUDA_TRY(cudaStreamWaitEvent(st, hp.done_in[s], 0));
+        if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(st, hp.done_out[s], 0));
+        DGT_TRY(run(hp.src[s].p, hp.dst[s].p, nb));
+        CUDA_TRY(cudaEventRecord(hp.done_exec[s], st));
+        CUDA_TRY(cudaStreamWaitEvent(hp.out, hp.done_exec[s], 0));
+        CUDA_TRY(cudaMemcpyAsync((char*)out_h + (size_t)(i * ch) * bout, hp.dst[s].p, (size_t)nb * bout,
+                                 cudaMemcpyDeviceToHost, hp.out));
+        CUDA_TRY(cudaEventRecord(hp.done_out[s], hp.out));
+    }
+    CUDA_TRY(cudaEventRecord(hp.last, hp.out));
+    CUDA_TRY(cudaStreamWaitEvent(st, hp.last, 0));
+    return DGT_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // extern "C"
 // ---------------------------------------------------------------------------------------
 extern "C" {
@@ -1573,6 +1650,29 @@ int dgt_workspace_bytes(dgt_plan_t plan, int64_t batch, size_t* bytes) {
     if (!plan || !bytes || batch < 0) return fail(DGT_ERR_ARG, "bad argument");
     *bytes = kWsHeader + plan->ws_bytes(batch);
     return DGT_OK;
+}
+
+int dgt_exec_host(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, int64_t chunk, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    const PlanCore& k = plan->core;
+    const size_t rs = k.precision == DGT_F64 ? sizeof(double) : sizeof(float);
+    const size_t bin = (f_is_real ? rs : 2 * rs) * (size_t)k.L, bout = 2 * rs * (size_t)k.N * (size_t)k.M;
+    cudaStream_t st = (cudaStream_t)stream;
+    return host_pipeline(plan, f, bin, c, bout, batch, chunk, st, [&](const void* din, void* dout, int64_t nb) {
+        return plan->exec(din, f_is_real, dout, nb, nullptr, st);
+    });
+}
+
+int idgt_exec_host(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,
+                   int64_t chunk, void* stream) {
+    if (!plan || (!f && batch) || (!c && batch)) return fail(DGT_ERR_ARG, "null pointer");
+    const PlanCore& k = plan->core;
+    const size_t rs = k.precision == DGT_F64 ? sizeof(double) : sizeof(float);
+    const size_t bin = 2 * rs * (size_t)k.N * (size_t)k.M, bout = (f_real_out ? rs : 2 * rs) * (size_t)k.L;
+    cudaStream_t st = (cudaStream_t)stream;
+    return host_pipeline(plan, c, bin, f, bout, batch, chunk, st, [&](const void* din, void* dout, int64_t nb) {
+        return plan->iexec(din, dout, f_real_out, nb, which_window, nullptr, plan->expired, st);
+    });
 }
 
 int dgt_exec_ws(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, void* workspace, void* stream) {
