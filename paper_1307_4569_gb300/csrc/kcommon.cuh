@@ -96,6 +96,7 @@ struct Sh1Row {
     uint32_t Bq;       // C4 n mod 2N
     uint32_t Kc;       // C6 n mod L
     uint32_t n2;       // n mod 2N
+    uint32_t al, be;   // n2 Bq and n2 C5 mod 2N: the phase term n2 (Bq + C5 k) = al + be k
     int64_t base;      // b N M
 };
 template <typename C> __device__ __forceinline__ Sh1Row sh1_row(const PostParams<C>& pp, int64_t b, int64_t n) {
@@ -104,21 +105,52 @@ template <typename C> __device__ __forceinline__ Sh1Row sh1_row(const PostParams
     r.A = pp.q2N.mod(pp.f_C2 * r.n2);
     r.Bq = pp.q2N.mod(pp.f_C4 * r.n2);
     r.Kc = pp.qL.mod((uint32_t)((uint64_t)pp.f_C6 * (uint32_t)n % pp.qL.d));
+    r.al = pp.q2N.mod(r.n2 * r.Bq);
+    r.be = pp.q2N.mod(r.n2 * pp.f_C5);
     r.base = b * pp.N * pp.M;
     return r;
 }
+// the output time mt and channel kt of channel m of the row (the coefficient's offset is
+// base + mt M + kt), and the exponent e of its phase exp(2 pi i e / 2N) (pp.cis2N.at(e))
 template <typename C>
-__device__ __forceinline__ int64_t sh1_at(const PostParams<C>& pp, const Sh1Row& r, int m, C& ph) {
+__device__ __forceinline__ void sh1_index(const PostParams<C>& pp, const Sh1Row& r, int m, uint32_t& e, uint32_t& mt,
+                                          uint32_t& kt) {
     const uint32_t twoN = pp.q2N.d;
     const uint32_t k = m ? pp.f_Nr - (uint32_t)m : 0u;           // -kappa mod Nr
     const uint32_t k2 = pp.q2N.mod(k);
     const uint32_t sq1 = pp.q2N.mod(pp.f_C1 * k2 + r.A);
-    const uint32_t mt = sq1 >= pp.f_N ? sq1 - pp.f_N : sq1;
+    mt = sq1 >= pp.f_N ? sq1 - pp.f_N : sq1;
     const uint32_t t1 = pp.q2N.mod(pp.f_C3 * pp.q2N.mod(sq1 * sq1));
     const uint32_t inner = pp.q2N.mod(r.Bq + pp.f_C5 * k2);
     const uint32_t t2 = pp.q2N.mod(r.n2 * inner);
-    ph = pp.cis2N.at(t1 >= t2 ? t1 - t2 : t1 + twoN - t2);
-    const uint32_t kt = pp.qb.div(pp.qL.mod(pp.f_s1ar * pp.qL.mod(k) + r.Kc));
+    e = t1 >= t2 ? t1 - t2 : t1 + twoN - t2;
+    kt = pp.qb.div(pp.qL.mod(pp.f_s1ar * pp.qL.mod(k) + r.Kc));
+}
+// sh1_index for the rows whose output channel is known (s1 = 0: the tile kernels): the time mt
+// and the phase exponent e only, with k < Nr <= N < 2N its own residue, and the quadratic term
+// skipped when C3 = 0 (same values)
+template <typename C>
+__device__ __forceinline__ void sh1_index_t(const PostParams<C>& pp, const Sh1Row& r, int m, uint32_t& e,
+                                            uint32_t& mt) {
+    const uint32_t twoN = pp.q2N.d;
+    const uint32_t k = m ? pp.f_Nr - (uint32_t)m : 0u;
+    const uint32_t sq1 = pp.q2N.mod(pp.f_C1 * k + r.A);
+    mt = sq1 >= pp.f_N ? sq1 - pp.f_N : sq1;
+    const uint32_t t1 = pp.f_C3 ? pp.q2N.mod(pp.f_C3 * pp.q2N.mod(sq1 * sq1)) : 0u;
+    const uint32_t t2 = pp.q2N.mod(r.al + r.be * k);
+    e = t1 >= t2 ? t1 - t2 : t1 + twoN - t2;
+}
+template <typename C>
+__device__ __forceinline__ void sh1_split(const PostParams<C>& pp, const Sh1Row& r, int m, C& ph, uint32_t& mt,
+                                          uint32_t& kt) {
+    uint32_t e;
+    sh1_index(pp, r, m, e, mt, kt);
+    ph = pp.cis2N.at(e);
+}
+template <typename C>
+__device__ __forceinline__ int64_t sh1_at(const PostParams<C>& pp, const Sh1Row& r, int m, C& ph) {
+    uint32_t mt, kt;
+    sh1_split(pp, r, m, ph, mt, kt);
     return r.base + (int64_t)mt * pp.M + kt;
 }
 

@@ -115,6 +115,125 @@ __global__ void __launch_bounds__(MrRow<F>::THREADS) pre_ifft_mr(const cplx<T>* 
 }
 
 // ------------------------------------------------------------------------------------
+// Frequency-shear rows in tiles.  When s1 = 0 and b is a multiple of C6, the output channel
+// of Algorithm 1's reindex, kt = (C6 n mod L) / b = n / q with q = b / C6, depends on the row n
+// alone, q rows make up one channel and N = q Nr.  A CTA then takes RT = q W consecutive rows of
+// one signal, i.e. W whole output channels kt0 .. kt0 + W - 1.
+//   fft_post_mr_tile: the rows' outputs, times their phases, go to shared memory by
+//   destination (stage[mt W + kt - kt0]) and leave as runs of W channels per output time:
+//   whole 32-byte sectors instead of one sector per 8-byte store.
+//   pre_ifft_mr_tile: the W channels are read the same way, and each transform gathers its
+//   inputs (times the conjugate phases) from shared memory.
+// Same values as fft_post_mr / pre_ifft_mr with SH1 (sh1_split is sh1_at's map).
+// ------------------------------------------------------------------------------------
+// the two-level table of exp(2 pi i e / 2N) (pp.cis2N: hi[e >> shift], lo[e mod 2^shift]) copied
+// into shared memory, so that the per-coefficient phase of the map is two shared loads; entries
+// rounded up to an even count, which keeps what follows 16-byte aligned
+template <typename C> struct SharedCis {
+    const C* hi;
+    const C* lo;
+    int shift;
+    __device__ __forceinline__ C at(uint32_t e) const { return cmul(hi[e >> shift], lo[e & ((1u << shift) - 1u)]); }
+};
+template <typename C> __host__ __device__ __forceinline__ uint32_t shared_cis_entries(const CisTable<C>& t) {
+    const uint32_t nhi = (uint32_t)(t.md.d >> t.shift) + 1u;
+    return (nhi + (1u << t.shift) + 1u) & ~1u;
+}
+template <typename C> __device__ __forceinline__ SharedCis<C> load_shared_cis(const CisTable<C>& t, C* buf) {
+    const uint32_t nhi = (uint32_t)(t.md.d >> t.shift) + 1u, nlo = 1u << t.shift;
+    for (uint32_t i = threadIdx.x; i < nhi; i += blockDim.x) buf[i] = t.hi[i];
+    for (uint32_t i = threadIdx.x; i < nlo; i += blockDim.x) buf[nhi + i] = t.lo[i];
+    return SharedCis<C>{buf, buf + nhi, t.shift};
+}
+
+template <typename T, class F, int W>
+__global__ void __launch_bounds__(1024) fft_post_mr_tile(const cplx<T>* __restrict__ y, cplx<T>* __restrict__ c,
+                                                         int64_t rows_per_signal, int q,
+                                                         const cplx<T>* __restrict__ tw, PostParams<cplx<T>> pp) {
+    using C = cplx<T>;
+    constexpr int NR = F::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int RT = q * W;
+    const int gi = threadIdx.x / F::G, t = threadIdx.x % F::G;
+    C* tab = reinterpret_cast<C*>(smem_raw);
+    const SharedCis<C> cis = load_shared_cis(pp.cis2N, tab);
+    C* stage = tab + shared_cis_entries(pp.cis2N);
+    C* sm = stage + gi * F::SMEM;
+    __syncthreads();
+    const int64_t tiles = rows_per_signal / RT;
+    const int64_t b = blockIdx.x / tiles;
+    const int64_t n0 = (blockIdx.x - b * tiles) * RT;
+    const int64_t nn = n0 + gi;
+    const uint32_t kt0 = (uint32_t)(n0 / q);
+    const int jj = gi / q;                         // this row's channel, kt - kt0
+    const C* yr = y + (b * rows_per_signal + nn) * NR;
+    const Sh1Row sr = sh1_row(pp, b, nn);
+    C v[F::V];
+    fft_mr<F, -1, 1>(0, t, sm, tw, [&](int k) -> C { return yr[k]; }, v);
+    // the transforms' last exchange reads came before their final barrier: the buffer is free
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i) {
+        if (!mr_out_ok<F>(t, i)) continue;
+        uint32_t e, mt;
+        sh1_index_t(pp, sr, mr_out_pos<F>(t, i), e, mt);
+        stage[mt * W + jj] = cmul(v[i], cis.at(e));
+    }
+    __syncthreads();
+    C* cb = c + sr.base + kt0;
+    const int total = (int)pp.f_N * W;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x)
+        cb[(int64_t)(idx / W) * pp.M + idx % W] = stage[idx];
+}
+
+template <typename T, class F, int W>
+__global__ void __launch_bounds__(1024) pre_ifft_mr_tile(const cplx<T>* __restrict__ c, cplx<T>* __restrict__ y,
+                                                         int64_t rows_per_signal, int q,
+                                                         const cplx<T>* __restrict__ tw, PostParams<cplx<T>> pp) {
+    using C = cplx<T>;
+    constexpr int NR = F::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int RT = q * W;
+    const int gi = threadIdx.x / F::G, t = threadIdx.x % F::G;
+    C* tab = reinterpret_cast<C*>(smem_raw);
+    const SharedCis<C> cis = load_shared_cis(pp.cis2N, tab);
+    C* stage = tab + shared_cis_entries(pp.cis2N);
+    C* sm = stage + (size_t)pp.f_N * W + gi * F::SMEM;
+    const int64_t tiles = rows_per_signal / RT;
+    const int64_t b = blockIdx.x / tiles;
+    const int64_t n0 = (blockIdx.x - b * tiles) * RT;
+    const int64_t nn = n0 + gi;
+    const uint32_t kt0 = (uint32_t)(n0 / q);
+    const int jj = gi / q;                         // this row's channel, kt - kt0
+    const Sh1Row sr = sh1_row(pp, b, nn);
+    const C* cb = c + sr.base + kt0;
+    const int total = (int)pp.f_N * W;
+    // the tile, eight loads in flight per thread
+    constexpr int U = 8;
+    for (int i0 = threadIdx.x; i0 < total; i0 += U * (int)blockDim.x) {
+        C x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = i0 + u * (int)blockDim.x;
+            x[u] = idx < total ? cb[(int64_t)(idx / W) * pp.M + idx % W] : mk((T)0, (T)0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * (int)blockDim.x < total) stage[i0 + u * (int)blockDim.x] = x[u];
+    }
+    __syncthreads();
+    C v[F::V];
+    fft_mr<F, +1, 1>(0, t, sm, tw, [&](int m) -> C {
+        uint32_t e, mt;
+        sh1_index_t(pp, sr, m, e, mt);
+        return cmulc(stage[mt * W + jj], cis.at(e));
+    }, v);
+    C* yr = y + (b * rows_per_signal + nn) * NR;
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i)
+        if (mr_out_ok<F>(t, i)) yr[mr_out_pos<F>(t, i)] = v[i];
+}
+
+// ------------------------------------------------------------------------------------
 // column kernels (transforms along the strided dimension, W adjacent columns per CTA): the
 // Zak transform, the block product with the inverse FFT over xi, its adjoint, and the inverse
 // Zak transform -- the arithmetic of zak_fwd_p2, prod_ifft_p2, fft_prod_adj_p2, zak_inv_p2
@@ -299,6 +418,26 @@ cudaError_t mr_rows_n(const cplx<T>* src, cplx<T>* dst, const SepGeom& g, int64_
     using RC = MrRow<F>;
     const size_t smem = sizeof(cplx<T>) * (size_t)F::SMEM * RC::RPB;
     const bool sh1 = pp.mode == POST_SHEAR1;
+    if (sh1 && pp.sh1_fast && pp.f_s1ar == 0 && J == 1 && pp.f_C6 > 0 && pp.qb.d % pp.f_C6 == 0) {
+        // tiles of q W rows = W whole output channels (see fft_post_mr_tile): every condition
+        // that keeps the tile's channels in [kt0, kt0 + W) and its stage inside shared memory
+        constexpr int W = 2;
+        const int64_t q = pp.qb.d / pp.f_C6;
+        const int64_t rps = g.d * g.q;                 // rows per signal
+        const int64_t RT = q * W;
+        const size_t stage = sizeof(cplx<T>) * (size_t)pp.f_N * W;
+        const size_t fsm = sizeof(cplx<T>) * (size_t)F::SMEM * (size_t)RT;
+        const size_t tsm = sizeof(cplx<T>) * (size_t)shared_cis_entries(pp.cis2N) + (POST ? std::max(stage, fsm) : stage + fsm);
+        if ((int64_t)pp.f_N == q * F::N && rps % RT == 0 && rps / q <= (int64_t)pp.f_M &&
+            (uint64_t)pp.f_C6 * (uint64_t)(rps - 1) < (uint64_t)pp.qL.d && RT * F::G <= 1024 && tsm <= kSmemBudget) {
+            auto kt = POST ? fft_post_mr_tile<T, F, W> : pre_ifft_mr_tile<T, F, W>;
+            cudaError_t e = p2_smem(kt, tsm);
+            if (e != cudaSuccess) return e;
+            kt<<<(unsigned)(B * (rps / RT)), (unsigned)(RT * F::G), tsm, st>>>(src, dst, rps, (int)q,
+                                                                           (const cplx<T>*)tw, pp);
+            return cudaGetLastError();
+        }
+    }
     auto k = POST ? (sh1 ? fft_post_mr<T, F, true> : fft_post_mr<T, F, false>)
                   : (sh1 ? pre_ifft_mr<T, F, true> : pre_ifft_mr<T, F, false>);
     cudaError_t e = p2_smem(k, smem);
