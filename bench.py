@@ -971,6 +971,9 @@ def main():
     ap.add_argument("--lambda-sweep", action="store_true",
                     help="run only the coset / shear timing sweep over lambda2 = 1..10 (Fig. 2 setups) and "
                          "print its rows as one JSON line")
+    ap.add_argument("--dense-third", choices=["coset", "shear"], default=None,
+                    help="run only the lambda = 1/3 float32 step (128 signals, analysis + dual synthesis) on this "
+                         "route, --steps times after 2 warm-up steps, and print one JSON line")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the serving run (Poisson 2000 requests/s); 0 skips it")
     args = ap.parse_args()
@@ -990,6 +993,26 @@ def main():
                                                                    "p99_ms", "max_ms", "peak_inflight_bytes",
                                                                    "mean_batch")}})
         print(json.dumps({"serve_sweep": rows}), flush=True)
+        return
+    if args.dense_third:
+        import numpy as np
+        import torch
+
+        from paper_1307_4569_gb300 import Plan
+        from paper_1307_4569_gb300 import build as bld
+        from workloads import DENSE_THIRD, gaussian_window, signal_batch
+
+        bld.build()
+        w, dev = DENSE_THIRD, torch.device("cuda", 0)
+        f = torch.from_numpy(signal_batch(w, cfg_id=2).astype(np.complex64)).to(dev)
+        c = torch.empty((w.batch, w.N, w.M), dtype=torch.complex64, device=dev)
+        fr = torch.empty_like(f)
+        p = Plan(w.L, w.a, w.M, w.lam1, w.lam2, gaussian_window(w.L), route=args.dense_third, precision="f32")
+        p.dual_window()
+        ms = _time_cuda(lambda: (p.dgt(f, out=c), p.idgt(c, window="dual", out=fr)), args.steps)
+        err = float(torch.linalg.vector_norm(fr - f) / torch.linalg.vector_norm(f))
+        print(json.dumps({"dense_third": {"workload": w.name, "route": args.dense_third, "ms_per_step": ms,
+                                          "reconstruction_rel_err": err, "plan": p.info}}), flush=True)
         return
     if args.lambda_sweep:
         import torch
