@@ -192,8 +192,9 @@ int idgt_exec_real(dgt_plan_t plan, const void* c, void* f, int64_t batch, int w
  * copy; with pinned (page-locked) host buffers it returns before the copies end, so
  * synchronise `stream` before reading the output.  Pageable buffers work, with copies that
  * block the host.  The staging slots grow to 2 chunks of input and output and stay with the
- * plan.  One call at a time per plan.  Errors: DGT_ERR_ARG (null pointer, negative batch or
- * chunk), and those of dgt_exec / idgt_exec. */
+ * plan.  One call at a time per plan, with the plan's device current.  Errors: DGT_ERR_ARG
+ * (null pointer, negative batch or chunk, another device current), and those of dgt_exec /
+ * idgt_exec. */
 int dgt_exec_host(dgt_plan_t plan, const void* f, int f_is_real, void* c, int64_t batch, int64_t chunk,
                   void* stream);
 int idgt_exec_host(dgt_plan_t plan, const void* c, void* f, int f_real_out, int64_t batch, int which_window,

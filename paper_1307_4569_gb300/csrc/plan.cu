@@ -1482,6 +1482,10 @@ static int host_pipeline(dgt_plan_t plan, const void* in_h, size_t bin, void* ou
                          const std::function<int(const void*, void*, int64_t)>& run) {
     if (batch <= 0) return batch == 0 ? DGT_OK : fail(DGT_ERR_ARG, "negative batch");
     if (chunk < 0) return fail(DGT_ERR_ARG, "negative chunk");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (plan->core.device >= 0 && dev != plan->core.device)
+        return fail(DGT_ERR_ARG, "the current device (%d) is not the plan's (%d)", dev, plan->core.device);
     DGT_TRY(plan->pending_expiry());
     if (!plan->host_pipe) plan->host_pipe.reset(new HostPipe());
     HostPipe& hp = *plan->host_pipe;
