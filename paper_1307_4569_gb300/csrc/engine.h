@@ -239,6 +239,19 @@ cudaError_t mr_fft_prod_adj(const cplx<T>* y, const cplx<T>* zg, int64_t J, cplx
 template <typename T>
 cudaError_t mr_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, int64_t dbs, int64_t d, int64_t K0,
                        const void* tw, const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t mr_fftL_cols(const void* src, int src_real, cplx<T>* tmp, int64_t L1, int64_t L2, int dir, const void* tw,
+                         const ChirpParams<cplx<T>>& pre, const CisTable<cplx<T>>& cisL, int64_t B, cudaStream_t st);
+template <typename T>
+cudaError_t mr_fftL_rows(const cplx<T>* tmp, void* dst, int dst_real, int64_t L1, int64_t L2, int dir, const void* tw,
+                         const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st);
+// the lengths with a compiled mixed-radix transform (the cases of MR_SWITCH in kernels_mr.cuh)
+inline bool mr_compiled_len(int64_t n) {
+    switch (n) {
+        case 60: case 120: case 180: case 240: case 360: case 480: case 720: case 960: case 2160: return true;
+        default: return false;
+    }
+}
 // Bounded device waits (the tensor-copy staging of fft_prod_adj): the wait limit in clock
 // cycles that launches pass to the kernels (a test hook lowers it).  A CTA whose wait expires
 // sets the caller's word `expired` to 1 (a plan's host-mapped word, or the word at the start

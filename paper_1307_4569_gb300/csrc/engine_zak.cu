@@ -635,6 +635,10 @@ template <typename T>
 cudaError_t launch_fftL_cols(const void* src, int src_real, cplx<T>* tmp, int64_t L1, int64_t L2, int dir,
                              const FftRef& f1, const ChirpParams<cplx<T>>& pre, const CisTable<cplx<T>>& cisL,
                              int64_t B, cudaStream_t st) {
+    {
+        cudaError_t e = mr_fftL_cols<T>(src, src_real, tmp, L1, L2, dir, f1.tw, pre, cisL, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using C = cplx<T>;
     const int64_t cap = tile_cap<T>();
     if (L1 > cap) return cudaErrorInvalidValue;
@@ -653,6 +657,10 @@ template <typename T>
 cudaError_t launch_fftL_rows(const cplx<T>* tmp, void* dst, int dst_real, int64_t L1, int64_t L2, int dir,
                              const FftRef& f2, const ChirpParams<cplx<T>>& post, T scale, int64_t B,
                              cudaStream_t st) {
+    {
+        cudaError_t e = mr_fftL_rows<T>(tmp, dst, dst_real, L1, L2, dir, f2.tw, post, scale, B, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using C = cplx<T>;
     const int64_t cap = tile_cap<T>();
     if (L2 + 1 > cap) return cudaErrorInvalidValue;

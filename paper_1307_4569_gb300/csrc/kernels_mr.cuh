@@ -385,6 +385,83 @@ __global__ void __launch_bounds__(MrCol<T, F>::THREADS) zak_inv_mr(const cplx<T>
 }
 
 // ------------------------------------------------------------------------------------
+// The length-L transform of the frequency-shear branch as four steps, L = L1 L2, with compiled
+// transforms of both factors (the arithmetic of fftL_cols_kernel / fftL_rows_kernel):
+//   cols: DFT over n1 of x[n1 L2 + n2] (pre-chirp on load), times exp(dir 2 pi i n2 k1 / L),
+//         into tmp[k1 L2 + n2]; W columns n2 per CTA.  n2 k1 < L needs no reduction.
+//   rows: DFT over n2 of tmp[k1 L2 + .] per row k1, into dst[k1 + L1 k2] scaled and
+//         post-chirped; the rows of a CTA go through shared memory so that the transposed
+//         store writes runs of consecutive k1.
+// ------------------------------------------------------------------------------------
+template <typename T, class F, int DIR>
+__global__ void __launch_bounds__(MrCol<T, F>::THREADS) fftL_cols_mr(const void* __restrict__ src, int src_real,
+                                                                     cplx<T>* __restrict__ tmp, int64_t L2,
+                                                                     const cplx<T>* __restrict__ tw,
+                                                                     ChirpParams<cplx<T>> pre, CisTable<cplx<T>> cisL) {
+    using C = cplx<T>;
+    using CF = MrCol<T, F>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int c = threadIdx.x % CF::W, t = threadIdx.x / CF::W;
+    const int64_t b = blockIdx.y;
+    const int64_t L = (int64_t)F::N * L2;
+    const int64_t col = (int64_t)blockIdx.x * CF::W + c;
+    const bool ok = col < L2;
+    C v[F::V];
+    fft_mr<F, DIR, CF::W>(c, t, sm, tw, [&](int e) -> C {
+        if (!ok) return mk((T)0, (T)0);
+        const int64_t l = col + L2 * e;
+        C x = load_any<C>(src, src_real, b * L + l);
+        if (pre.mode == PRE_CHIRP) x = cmul(x, chirp_factor(pre, l));
+        return x;
+    }, v);
+    if (!ok) return;
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i) {
+        if (!mr_out_ok<F>(t, i)) continue;
+        const int64_t k1 = mr_out_pos<F>(t, i);
+        const uint64_t ex = (uint64_t)(col * k1);
+        const C w = cisL.at(DIR < 0 ? (ex ? (uint64_t)L - ex : 0) : ex);
+        tmp[b * L + k1 * L2 + col] = cmul(v[i], w);
+    }
+}
+
+template <typename T, class F, int DIR>
+__global__ void __launch_bounds__(MrRow<F>::THREADS) fftL_rows_mr(const cplx<T>* __restrict__ tmp, void* __restrict__ dst,
+                                                                  int dst_real, int64_t L1,
+                                                                  const cplx<T>* __restrict__ tw,
+                                                                  ChirpParams<cplx<T>> post, T scale) {
+    using C = cplx<T>;
+    using RC = MrRow<F>;
+    constexpr int L2 = F::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / F::G, t = threadIdx.x % F::G;
+    C* sm = reinterpret_cast<C*>(smem_raw) + gi * F::SMEM;
+    C* stage = reinterpret_cast<C*>(smem_raw);                 // [k2][RPB] after the transforms
+    const int64_t b = blockIdx.y;
+    const int64_t L = L1 * L2;
+    const int64_t r0 = (int64_t)blockIdx.x * RC::RPB;
+    const int64_t r = r0 + gi;
+    const bool ok = r < L1;
+    C v[F::V];
+    fft_mr<F, DIR, 1>(0, t, sm, tw, [&](int k) -> C { return ok ? tmp[b * L + r * L2 + k] : mk((T)0, (T)0); }, v);
+    // the transforms' last exchange reads came before their final barrier: the buffer is free
+#pragma unroll
+    for (int i = 0; i < F::OUT; ++i)
+        if (mr_out_ok<F>(t, i)) stage[mr_out_pos<F>(t, i) * RC::RPB + gi] = v[i];
+    __syncthreads();
+    const int nr = (int)min((int64_t)RC::RPB, L1 - r0);
+    for (int idx = threadIdx.x; idx < L2 * RC::RPB; idx += RC::THREADS) {
+        const int k2 = idx / RC::RPB, rr = idx % RC::RPB;
+        if (rr >= nr) continue;
+        const int64_t kk = r0 + rr + L1 * (int64_t)k2;
+        C x = cscale(stage[idx], scale);
+        if (post.mode == PRE_CHIRP) x = cmul(x, chirp_factor(post, kk));
+        store_any(dst, dst_real, b * L + kk, x);
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // the lengths with a compiled mixed-radix transform: N, threads per transform, radices
 // ------------------------------------------------------------------------------------
 using Mr60 = Mixed<60, 4, RadixList<4, 15>>;
@@ -517,6 +594,34 @@ cudaError_t mr_zak_inv(const cplx<T>* zf, int64_t zbs, void* dst, int dst_real, 
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((K0 + CF::W - 1) / CF::W), (unsigned)B);
         k<<<grid, CF::THREADS, CF::SMEM, st>>>(zf, zbs, dst, dst_real, dbs, K0, (const cplx<T>*)tw, post, scale);
+        return cudaGetLastError();
+    })
+}
+
+template <typename T>
+cudaError_t mr_fftL_cols(const void* src, int src_real, cplx<T>* tmp, int64_t L1, int64_t L2, int dir, const void* tw,
+                         const ChirpParams<cplx<T>>& pre, const CisTable<cplx<T>>& cisL, int64_t B, cudaStream_t st) {
+    MR_SWITCH(L1, {
+        using CF = MrCol<T, FF>;
+        auto k = dir < 0 ? fftL_cols_mr<T, FF, -1> : fftL_cols_mr<T, FF, +1>;
+        cudaError_t e = mr_col_prep<T, FF>(k);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((L2 + CF::W - 1) / CF::W), (unsigned)B);
+        k<<<grid, CF::THREADS, CF::SMEM, st>>>(src, src_real, tmp, L2, (const cplx<T>*)tw, pre, cisL);
+        return cudaGetLastError();
+    })
+}
+template <typename T>
+cudaError_t mr_fftL_rows(const cplx<T>* tmp, void* dst, int dst_real, int64_t L1, int64_t L2, int dir, const void* tw,
+                         const ChirpParams<cplx<T>>& post, T scale, int64_t B, cudaStream_t st) {
+    MR_SWITCH(L2, {
+        using RC = MrRow<FF>;
+        auto k = dir < 0 ? fftL_rows_mr<T, FF, -1> : fftL_rows_mr<T, FF, +1>;
+        const size_t smem = sizeof(cplx<T>) * (size_t)FF::SMEM * RC::RPB;
+        cudaError_t e = p2_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((L1 + RC::RPB - 1) / RC::RPB), (unsigned)B);
+        k<<<grid, RC::THREADS, smem, st>>>(tmp, dst, dst_real, L1, (const cplx<T>*)tw, post, scale);
         return cudaGetLastError();
     })
 }

@@ -1237,11 +1237,16 @@ static int create_plan(dgt_plan_t* out, int64_t L, int64_t a, int64_t M, int64_t
         k.C6 = (int64_t)(((__int128)k.sh.s0 * k.sh.s1 + 1) * br % L);
         k.sep = make_sep(L, br, k.Nr);
         k.J = 1;
-        // L = L1 L2, both transformable in one tile, as balanced as possible
-        int64_t b1 = 0;
+        // L = L1 L2, both transformable in one tile, as balanced as possible; a split into two
+        // lengths with compiled mixed-radix transforms is preferred when there is one
+        int64_t b1 = 0, bc = 0;
         for (int64_t x = 1; x * x <= L; ++x)
-            if (L % x == 0 && fft_ok(x, precision) && fft_ok(L / x, precision)) b1 = x;
+            if (L % x == 0 && fft_ok(x, precision) && fft_ok(L / x, precision)) {
+                b1 = x;
+                if (mr_compiled_len(x) && mr_compiled_len(L / x)) bc = x;
+            }
         if (b1 == 0) return fail(DGT_ERR_UNSUPPORTED, "FFT_L split of L=%lld unsupported", (long long)L);
+        if (bc) b1 = bc;
         k.L1 = b1;
         k.L2 = L / b1;
     }

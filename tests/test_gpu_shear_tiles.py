@@ -19,6 +19,7 @@ CASES = [
     (1920, 16, 48, 1, 2),      # q = 2, Nr = 60
     (7680, 32, 64, 1, 2),      # q = 2, Nr = 120
     (3840, 16, 48, 1, 4),      # q = 4, Nr = 60
+    (7200, 60, 720, 1, 2),     # q = 2, Nr = 60; L = 60 * 120, both length-L factors compiled
 ]
 
 
